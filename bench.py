@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the direct-sum Hermite force engine on one GB300 (or N replicas).
+
+Workload (default, the precision configuration): a Plummer sphere of
+N = 2^20 equal-mass particles, eps = 1/4096, shared block step dt = 2^-10 so
+that every block step is a full i = j evaluation.  One "step" is one whole
+block step of the hot path through the C ABI (nb_step): block selection,
+prediction of all N, mixed-precision forces on all N active particles from
+all N (N^2 = 1.1e12 pairwise interactions), Hermite correction and new steps.
+
+Printed (rank 0, one JSON line): interactions/s over the timed steps (all
+ranks), the force kernel's roofline against the FP32 CUDA-core peak
+(152 SMs x 128 lanes x 2 flop x 2070 MHz, 60 flop per interaction), an
+end-to-end number through the same C ABI with host buffers (H2D of the step's
+inputs and D2H of its results inside the timed region), the FP64 GPU path on
+the same state, the mixed path's error against the FP64 oracle on sampled
+particles, and the oracle timed on the host cores (cpu_baseline).
+
+``--impl reference`` times the oracle (the plain FP64 CPU direct sum) on the
+host cores for the same metric on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU; max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FLOP_PER_INTERACTION = 60
+SM_MAX_MHZ_FALLBACK = 2070.0
+METRIC = "force interactions/s"
+UNIT = "interactions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20, help="particles (default 2^20)")
+    ap.add_argument("--eps", type=float, default=1.0 / 4096)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="sampled i for the oracle legs")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp32_peak_tflops(sms, mhz):
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_reference(args, ws, rank):
+    """The oracle (plain FP64 CPU direct sum) on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_0709_4552_gb300 import inputs
+    oracle.build()
+    m, x, v = inputs.plummer(args.n, args.seed)
+    k = max(1, min(args.cpu_sample // 4, args.n))
+    idx = inputs.sample_indices(args.n, k, args.seed + 1000)
+    for _ in range(args.warmup):
+        oracle.forces(m, x, v, args.eps, idx=idx[: max(1, k // 8)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forces(m, x, v, args.eps, idx=idx)
+    dt = time.perf_counter() - t0
+    inter = float(k) * args.n * args.steps
+    val = inter / dt
+    cores = oracle.max_threads()
+    sample = f"{k} sampled active particles x all N={args.n} j per step (of the N x N block step)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Plummer sphere)",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"Plummer sphere N={args.n}, equal masses, eps=1/{round(1 / args.eps)}, "
+                        f"shared dt=2^-10 (every block step is a full i=j step of {args.precision} forces)",
+            "N": args.n, "n_active": args.n, "eps": args.eps, "precision": args.precision, "seed": args.seed,
+            "l2": "state read per step 0.35 GB > L2 (126 MB); L2 flushed (512 MB write) between steps"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_0709_4552_gb300 import build, inputs
+    build.build()
+    from paper_0709_4552_gb300 import nbody as nb
+
+    N, eps, dt_shared = args.n, args.eps, 2.0 ** -10
+    prec = nb.NB_MIXED if args.precision == "mixed" else nb.NB_FP64
+    m, x, v = inputs.plummer(N, args.seed)
+    stream = torch.cuda.current_stream(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    s = nb.NBody(N, prec, local, stream=stream)
+    s.set_params(eps, 0.01, dt_shared, dt_shared)
+    s.set_j_particles(0, m, x, v)
+    s.initial_forces_and_dt()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        s.step()
+    s.get_timings(reset=True)
+    launches0 = s.get_counters()["kernel_launches"]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        s.step()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    tim = s.get_timings()
+    launches = s.get_counters()["kernel_launches"] - launches0
+    t_max = ms
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    inter_rank = float(N) * N * args.steps
+    value = inter_rank * ws / (t_max / 1e3)
+
+    # roofline of the force kernel (events on the context's stream around each launch)
+    force_s_per_launch = tim["ms_force"] / 1e3 / args.steps
+    achieved_tflops = FLOP_PER_INTERACTION * float(N) * N / force_s_per_launch / 1e12
+    peak = fp32_peak_tflops(sms, SM_MAX_MHZ_FALLBACK)
+    sm_mhz = clk["sm_mhz"] if clk else None
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs,
+    # the step, D2H of its results, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        st = s.get_particles(0, N)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hin = dict(m=pin(st["m"]), x=pin(st["x"]), v=pin(st["v"]), a=pin(st["a"]), jerk=pin(st["jerk"]),
+                   t=pin(st["t"]), dt=pin(st["dt"]))
+        hout = {k: pin(np.empty_like(st[k])) for k in ("x", "v", "a", "jerk", "pot", "t", "dt")}
+        e_steps = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            s.set_j_particles(0, hin["m"], hin["x"], hin["v"], hin["a"], hin["jerk"], hin["t"], hin["dt"])
+            s.step()
+            s.get_particles(0, N, out=hout)
+        barrier()
+        e_s = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([e_s], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e_s = float(tt.item())
+        bi = sum(t.numel() * 8 for t in hin.values())
+        bo = sum(t.numel() * 8 for t in hout.values())
+        e2e = {"value": float(N) * N * e_steps * ws / e_s, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "steps": e_steps}
+
+    # FP64 GPU path and mixed-path accuracy on sampled particles of the same state
+    extra = {}
+    cpu = None
+    if rank == 0:
+        st = s.get_particles(0, N)
+        k = min(args.cpu_sample, N)
+        idx = inputs.sample_indices(N, k, args.seed + 1000).astype(np.int32)
+        t_now = float(st["t"][0])
+        s.predict(t_now)
+        am, jm, pm = s.compute_forces(idx)
+        s.set_precision(nb.NB_FP64)
+        s.predict(t_now)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a64, j64, p64 = s.compute_forces(idx)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_rate = float(k) * N / (e0.elapsed_time(e1) / 1e3)
+        s.set_precision(prec)
+        extra["fp64_gpu_path"] = {"value": fp64_rate, "unit": UNIT,
+                                  "sample": f"{k} active x N={N}", "vs_mixed": fp64_rate / value * ws}
+        if not args.no_cpu:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            ar, jr, pr = oracle.forces(st["m"], st["x"], st["v"], eps, idx=idx.astype(np.int64))
+            cpu_s = time.perf_counter() - t0
+            cpu = {"value": float(k) * N / cpu_s, "unit": UNIT, "cores": oracle.max_threads(),
+                   "kind": "oracle", "sample": f"forces on {k} sampled particles from all N={N} "
+                                               f"(one block step's state), {cpu_s:.1f} s"}
+
+            def rel(a, b):
+                return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+            ea, ej, ep = rel(am, ar), rel(jm, jr), np.abs(pm - pr) / np.abs(pr)
+            e64 = rel(a64, ar)
+            extra["accuracy_vs_oracle"] = {
+                "sample": k, "mixed_acc_median": float(np.median(ea)), "mixed_acc_max": float(ea.max()),
+                "mixed_jerk_median": float(np.median(ej)), "mixed_jerk_max": float(ej.max()),
+                "mixed_pot_median": float(np.median(ep)), "mixed_pot_max": float(ep.max()),
+                "fp64_acc_max": float(e64.max())}
+    s.close()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pairwise + f64 accumulate" if prec == nb.NB_MIXED else "f64",
+            "data": "synthetic (seeded Plummer sphere, Aarseth-Henon-Wielen sampling)",
+            "config": dict(workload_config(args), parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU"),
+            "gflops_60": value * FLOP_PER_INTERACTION / 1e9,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak, "traffic": None,
+                         "kernel": "force_mixed_kernel" if prec == nb.NB_MIXED else "force_fp64_kernel",
+                         "peak_basis": f"FP32 CUDA cores: {sms} SMs x 128 x 2 flop x {SM_MAX_MHZ_FALLBACK:.0f} MHz",
+                         "frac_at_sampled_clock": (achieved_tflops / fp32_peak_tflops(sms, sm_mhz)) if sm_mhz else None},
+            "phases_ms_per_step": {"predict": tim["ms_pred"] / args.steps, "force": tim["ms_force"] / args.steps,
+                                   "correct": tim["ms_corr"] / args.steps},
+            "gpu_launches": int(launches) * ws,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        out.update(extra)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

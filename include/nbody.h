@@ -1,0 +1,286 @@
+/*
+ * nbody.h -- C ABI of libnbody, a GB300 (sm_103a) direct-sum Hermite N-body
+ * force engine.
+ *
+ * The calls follow the paper's statement of one integration step (Groen,
+ * Portegies Zwart, McMillan & Makino, "Distributed N-body Simulation on the
+ * Grid Using Dedicated Hardware", Sec. 4.1 steps 1-7 and, for the split
+ * between predicting all particles and computing forces on an active block,
+ * Sec. 4.4 steps 2-7):
+ *   set j-particles -> next block time + active block -> predict all N to t
+ *   -> forces (acceleration, jerk, potential) on the active block from all N
+ *   -> correct the block and choose new power-of-two time steps.
+ *
+ * Conventions (every entry point):
+ *  - Returns NB_OK (0) or a negative NB_E* code; no exception or signal ever
+ *    crosses the ABI.  The first error is also kept in the context ("sticky")
+ *    and returned by nb_last_error until nb_clear_error.
+ *  - The caller owns every pointer it passes.  The library copies inputs in
+ *    and writes into caller-owned outputs; it keeps no caller pointer after
+ *    the call returns.
+ *  - ptr_kind says where caller buffers live: NB_PTR_HOST (pageable or pinned
+ *    host memory; the call synchronises the context's stream before
+ *    returning) or NB_PTR_DEVICE (device memory of the context's device; the
+ *    work is enqueued on the context's stream and the call returns without
+ *    synchronising).
+ *  - Vectors are row-major [count][3] FP64 at the ABI; the library stores
+ *    them structure-of-arrays internally.
+ *  - Units: N-body units, G = 1.
+ *  - One context per host thread at a time (contexts are not thread-safe);
+ *    any number of contexts may coexist.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define NB_OK         0
+#define NB_EINVAL    -1   /* bad argument (null pointer, range, ordering)   */
+#define NB_ENOMEM    -2   /* device or host allocation failed               */
+#define NB_ECUDA     -3   /* a CUDA runtime call failed                     */
+#define NB_ENUMERIC  -4   /* NaN or Inf seen in a result                    */
+#define NB_EDTMIN    -5   /* a step criterion fell below dt_min (clamped)   */
+#define NB_ETIMEOUT  -6   /* a bounded device wait gave up                  */
+#define NB_ESTATE    -7   /* call out of order (e.g. forces before predict) */
+
+/* ---- force-path precision ---------------------------------------------- */
+#define NB_FP64   0  /* IEEE FP64 pairwise arithmetic                        */
+#define NB_MIXED  1  /* FP32 pairwise on double-single position differences,
+                        FP64 accumulation of FP32 partial sums               */
+
+/* ---- where caller buffers live ---------------------------------------- */
+#define NB_PTR_HOST    0
+#define NB_PTR_DEVICE  1
+
+typedef struct nb_ctx nb_ctx;   /* opaque, owned by the library */
+
+/*
+ * nb_create -- make a context for up to n_max particles on CUDA device
+ * `device`, working on `cuda_stream` (a cudaStream_t; NULL = a stream the
+ * library creates and owns).  precision: NB_FP64 or NB_MIXED (changeable
+ * with nb_set_precision).  Allocates all device memory the context needs up
+ * front (about 0.3 KB per particle).  Parameters start at the paper's values
+ * (Sec. 2): eps = 2^-8, dt in [2^-22, 2^-3], eta = 0.01.
+ * Errors: NB_EINVAL (out == NULL, n_max < 1, bad precision/device),
+ * NB_ENOMEM, NB_ECUDA.  On error *out is NULL.
+ */
+int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda_stream);
+
+/* nb_destroy -- free the context and everything it allocated (NULL is a no-op). */
+void nb_destroy(nb_ctx* ctx);
+
+/*
+ * nb_set_params -- softening length eps >= 0 (Plummer softening, the
+ * "softening parameter" of Sec. 2), accuracy parameter eta > 0 of the
+ * Aarseth step criterion, and the block-step range dt_min <= dt_max, both
+ * powers of two (Sec. 2: powers of two between 2^-22 and 2^-3).  dt_min ==
+ * dt_max gives shared (equal) steps.  Errors: NB_EINVAL.
+ */
+int nb_set_params(nb_ctx* ctx, double eps, double eta, double dt_min, double dt_max);
+
+/* nb_default_params -- the paper's defaults (no context needed, no GPU). */
+void nb_default_params(double* eps, double* eta, double* dt_min, double* dt_max);
+
+/* nb_set_precision -- switch the force path (NB_FP64 / NB_MIXED).  Errors: NB_EINVAL. */
+int nb_set_precision(nb_ctx* ctx, int precision);
+
+/*
+ * nb_set_j_particles -- Sec. 4.1 step 1 (read the snapshot): write particles
+ * [first, first + count) of the j-store.  m[count]; x, v, a, jerk [count][3];
+ * t, dt [count].  a, jerk, t, dt may be NULL (zero; call
+ * nb_initial_forces_and_dt before stepping).  The particle count N becomes
+ * max(N, first + count).  Errors: NB_EINVAL (range beyond n_max, NULL m/x/v,
+ * count < 0, non-finite value), NB_ECUDA.
+ */
+int nb_set_j_particles(nb_ctx* ctx, int64_t first, int64_t count, const double* m, const double* x,
+                       const double* v, const double* a, const double* jerk, const double* t,
+                       const double* dt, int ptr_kind);
+
+/* nb_set_n -- set the particle count N (<= n_max); particles >= N are ignored. */
+int nb_set_n(nb_ctx* ctx, int64_t n);
+
+/* nb_get_n -- current particle count N. */
+int nb_get_n(nb_ctx* ctx, int64_t* n);
+
+/*
+ * nb_get_particles -- Sec. 4.1 step 7 (write the output): copy particles
+ * [first, first + count) out.  Any output pointer may be NULL (skipped).
+ * pot is the potential from the last force evaluation of each particle.
+ * Errors: NB_EINVAL (range), NB_ECUDA.
+ */
+int nb_get_particles(nb_ctx* ctx, int64_t first, int64_t count, double* m, double* x, double* v,
+                     double* a, double* jerk, double* pot, double* t, double* dt, int ptr_kind);
+
+/*
+ * nb_next_block -- Sec. 4.1 step 2: the next system time
+ * t = min_i (t_i + dt_i) and the active block {i : t_i + dt_i == t} in
+ * ascending index order.  *t_next and *n_active are written (host);
+ * active_idx (host, capacity >= N, may be NULL) receives the indices.  The
+ * block also stays on the device for nb_step / nb_correct_block.
+ * Errors: NB_ESTATE (N == 0), NB_ECUDA.
+ */
+int nb_next_block(nb_ctx* ctx, double* t_next, int32_t* active_idx, int64_t* n_active);
+
+/*
+ * nb_predict -- Sec. 4.1 step 3 (Sec. 4.4 step 4 on GRAPE): Taylor-predict
+ * positions and velocities of all N particles to time t from (x, v, a,
+ * jerk, t_i).  FP64; the mixed path also gets double-single positions.
+ * Asynchronous on the context's stream.  Errors: NB_ESTATE, NB_ECUDA.
+ */
+int nb_predict(nb_ctx* ctx, double t);
+
+/*
+ * nb_compute_forces -- Sec. 4.1 step 4, Eq. 3 (t_force = tau_force n N):
+ * for each of the n active particles i_idx[k] (ascending, unique, < N),
+ * the Plummer-softened acceleration, jerk and potential summed over all
+ * j != i at the predicted positions/velocities of the last nb_predict:
+ *   acc_i  = sum_j m_j r_ij / s^3,
+ *   jerk_i = sum_j m_j [ v_ij / s^3 - 3 (r_ij . v_ij) r_ij / s^5 ],
+ *   pot_i  = - sum_j m_j / s,
+ * r_ij = x_j - x_i, v_ij = v_j - v_i, s^2 = |r_ij|^2 + eps^2.
+ * Outputs acc, jerk [n][3] and pot [n] (any may be NULL); the results are
+ * also kept for nb_correct.  i_idx and outputs are host or device per
+ * ptr_kind.  n == 0 is a no-op.  Errors: NB_EINVAL (n > N, index out of
+ * range or not ascending -- checked on the host for host indices),
+ * NB_ESTATE (no prediction), NB_ECUDA.
+ */
+int nb_compute_forces(nb_ctx* ctx, const int32_t* i_idx, int64_t n, double* acc, double* jerk,
+                      double* pot, int ptr_kind);
+
+/*
+ * nb_correct -- Sec. 4.1 step 5: 4th-order Hermite correction of the n
+ * particles i_idx (the list of the preceding nb_compute_forces) to time t,
+ * using their old (a, jerk) and the new ones; stores the new a, jerk, pot,
+ * t_i = t and a new block step dt_i: the Aarseth criterion with eta,
+ * rounded down to a power of two, clamped to [dt_min, dt_max], growing at
+ * most x2 and only when t is a multiple of 2 dt_old (Sec. 2 block steps).
+ * Errors: NB_EINVAL, NB_ESTATE (list differs from the force call), NB_ECUDA.
+ * NaN/Inf results and criterion underflows are recorded on the device and
+ * reported by nb_check_device_status.
+ */
+int nb_correct(nb_ctx* ctx, const int32_t* i_idx, int64_t n, double t, int ptr_kind);
+
+/*
+ * nb_initial_forces_and_dt -- Sec. 4.1 step 1 (initialise the N-body
+ * system): forces of all N at their current positions (t_i = 0), and
+ * initial steps dt_i = largest power of two <= eta |a| / |jerk|, clamped.
+ */
+int nb_initial_forces_and_dt(nb_ctx* ctx);
+
+/*
+ * nb_step -- one block step entirely on the device: next block (step 2),
+ * predict (3), forces (4), correct (5).  Writes the block time and size
+ * (host).  Errors as the calls it makes.
+ */
+int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
+
+/*
+ * nb_integrate -- Sec. 4.1 steps 2-6: block steps until every particle has
+ * reached t_end (t_end must be a multiple of dt_max).  use_graph != 0 runs
+ * the loop as one CUDA graph with a device-side while node (no host round
+ * trip per step).  Errors: NB_EINVAL, NB_ENUMERIC, NB_ECUDA.
+ */
+int nb_integrate(nb_ctx* ctx, double t_end, int use_graph);
+
+/*
+ * nb_energy -- kinetic and potential energy of the current state (the paper
+ * is silent on diagnostics): K = sum m v^2/2, W = (1/2) sum m_i phi_i with
+ * phi from a full i = j force evaluation in the context's precision.  Uses
+ * the state as stored (call when all t_i are equal).  Host outputs.
+ */
+int nb_energy(nb_ctx* ctx, double* ekin, double* epot);
+
+/*
+ * nb_get_timings -- accumulated device time (ms) of the predict, force and
+ * correct phases (Eq. 1: t_pred + t_force + t_corr per step) and the number
+ * of pairwise interactions (sum of n N over force calls) since the last
+ * reset; reset != 0 zeroes them after reading.  Any pointer may be NULL.
+ */
+int nb_get_timings(nb_ctx* ctx, double* ms_pred, double* ms_force, double* ms_corr,
+                   double* interactions, int reset);
+
+/*
+ * nb_get_counters -- kernels this context has launched (every library kernel,
+ * counted at launch) and block steps taken, since creation.  Host-only.
+ */
+int nb_get_counters(nb_ctx* ctx, int64_t* kernel_launches, int64_t* block_steps);
+
+/*
+ * nb_check_device_status -- synchronise and read the device-side status
+ * word: NaN/Inf seen (NB_ENUMERIC), step criterion below dt_min (count in
+ * *dt_underflows, may be NULL), bounded wait timeout (NB_ETIMEOUT).
+ */
+int nb_check_device_status(nb_ctx* ctx, int64_t* dt_underflows);
+
+/* nb_last_error / nb_clear_error -- the sticky first error of a context. */
+int nb_last_error(nb_ctx* ctx);
+void nb_clear_error(nb_ctx* ctx);
+
+/*
+ * nb_set_tuning -- override the force launch: i per thread (1,2,4),
+ * threads per CTA (64..512), j-tile (32..1024), split-j factor (0 = auto).
+ * 0 for any argument restores the automatic choice (autotuner table).
+ * Errors: NB_EINVAL (unsupported combination).
+ */
+int nb_set_tuning(nb_ctx* ctx, int i_per_thread, int threads, int j_tile, int n_split);
+
+/*
+ * nb_autotune -- time the supported force launches for the current N and
+ * active-block size n on the current state (needs a prediction) and keep the
+ * fastest for blocks of about that size.  Writes the chosen configuration
+ * (any pointer may be NULL).
+ */
+int nb_autotune(nb_ctx* ctx, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split);
+
+/* ---- batched ensemble of independent clusters --------------------------- */
+/*
+ * nb_ensemble_create -- a context for n_clusters independent systems stored
+ * back to back: cluster c owns particles [offsets[c], offsets[c+1]) of one
+ * j-store (offsets host, ascending, offsets[0] == 0).  eps[c] is each
+ * cluster's softening (host).  Fill it with nb_set_j_particles on the whole
+ * range, then nb_initial_forces_and_dt.  Errors: NB_EINVAL, NB_ENOMEM.
+ */
+int nb_ensemble_create(nb_ctx** out, int32_t n_clusters, const int64_t* offsets, const double* eps,
+                       int precision, int device, void* cuda_stream);
+
+#define NB_ENSEMBLE_PERSISTENT   0  /* one graph launch: every cluster's block
+                                       steps as device-driven batched steps   */
+#define NB_ENSEMBLE_PER_CLUSTER  1  /* reference: clusters one after another,
+                                       host-driven per-step kernel launches   */
+
+/*
+ * nb_ensemble_initial_forces_and_dt -- Sec. 4.1 step 1 for every cluster:
+ * forces of all particles within their own cluster at t = 0, initial steps.
+ * (nb_initial_forces_and_dt on an ensemble context calls this.)
+ */
+int nb_ensemble_initial_forces_and_dt(nb_ctx* ctx);
+
+/*
+ * nb_ensemble_integrate -- integrate every cluster to t_end with its own
+ * block steps (Sec. 4.1 steps 2-6 per cluster; t_end a multiple of dt_max).
+ * mode: NB_ENSEMBLE_*.  Both modes give the same block schedule.
+ */
+int nb_ensemble_integrate(nb_ctx* ctx, double t_end, int mode);
+
+/*
+ * nb_ensemble_energy -- kinetic and potential energy of every cluster (host
+ * arrays of n_clusters), each cluster's potential from its own particles.
+ */
+int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
+
+/* nb_strerror -- static text for a status code (never NULL). */
+const char* nb_strerror(int code);
+
+/* nb_version -- library version string (never NULL). */
+const char* nb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

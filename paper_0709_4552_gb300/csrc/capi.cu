@@ -1,0 +1,690 @@
+// capi.cu -- the extern "C" entry points of libnbody (declared and
+// documented in include/nbody.h): context lifetime, particle I/O, and the
+// block-step sequence of Sec. 4.1 (select -> predict -> forces -> correct).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "nb_internal.cuh"
+
+namespace {
+
+constexpr double kDefaultEps = 1.0 / 256.0;        // Sec. 2: softening 2^-8
+constexpr double kDefaultEta = 0.01;
+constexpr double kDefaultDtMin = 1.0 / 4194304.0;  // Sec. 2: 2^-22
+constexpr double kDefaultDtMax = 0.125;            // Sec. 2: 2^-3
+constexpr size_t kPinnedBytes = 1 << 16;
+
+int fail(nb_ctx* c, int code) {
+  if (c && c->last_error == NB_OK && code != NB_OK) c->last_error = code;
+  return code;
+}
+
+#define NB_CUDA(c, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      return fail((c), e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA); \
+    }                                                     \
+  } while (0)
+
+bool is_pow2(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return false;
+  int e;
+  return frexp(x, &e) == 0.5;
+}
+
+int select_device(nb_ctx* c) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return NB_ECUDA;
+  if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess) return NB_ECUDA;
+  return NB_OK;
+}
+
+#define NB_ENTER(c)                              \
+  do {                                           \
+    if (!(c)) return NB_EINVAL;                  \
+    if (select_device(c) != NB_OK) return fail((c), NB_ECUDA); \
+  } while (0)
+
+// entry points whose physics treats the j-store as ONE system
+#define NB_SINGLE(c)                                             \
+  do {                                                           \
+    NB_ENTER(c);                                                 \
+    if ((c)->n_clusters > 0) return fail((c), NB_ESTATE);        \
+  } while (0)
+
+void free_ctx(nb_ctx* c) {
+  if (!c) return;
+  void* dptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->jA, c->jB,
+                   c->jC, c->F, c->part, c->act, c->ident, c->ulist, c->sel_min, c->sel_cnt, c->red,
+                   c->status, c->d_offsets, c->d_ceps};
+  for (void* p : dptrs)
+    if (p) cudaFree(p);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  for (int i = 0; i < 8; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  free(c->h_offsets);
+  free(c->h_ceps);
+  free(c);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+bool host_list_ok(const int32_t* l, int64_t n, int64_t N) {
+  for (int64_t k = 0; k < n; ++k) {
+    if (l[k] < 0 || l[k] >= N) return false;
+    if (k > 0 && l[k - 1] >= l[k]) return false;
+  }
+  return true;
+}
+
+nb_tuning pick_tuning(const nb_ctx* c, int64_t n) {
+  const nb_tuning& o = c->tune_override;
+  if (o.ipt || o.threads || o.jtile || o.nsplit) {
+    nb_tuning d = nb_default_tuning(c->precision);
+    nb_tuning t{o.ipt ? o.ipt : d.ipt, o.threads ? o.threads : d.threads, o.jtile ? o.jtile : d.jtile,
+                o.nsplit};
+    if (nb_tuning_supported(c->precision, t)) return t;
+  }
+  for (int i = 0; i < c->tune_count; ++i) {
+    const nb_tune_entry& e = c->tune_table[i];
+    if (n >= e.n_lo && n < e.n_hi && nb_tuning_supported(c->precision, e.cfg)) return e.cfg;
+  }
+  nb_tuning t = nb_default_tuning(c->precision);
+  if (c->precision == NB_MIXED) {
+    // small active blocks: fewer i per CTA so that the split-j grid stays full
+    if (n <= 2048) t.ipt = 1;
+    else if (n <= 32768) t.ipt = 2;
+  }
+  return t;
+}
+
+// device view of a caller's list (copied to ulist for host lists)
+int stage_list(nb_ctx* c, const int32_t* list, int64_t n, int ptr_kind, const int32_t** d_list) {
+  if (ptr_kind == NB_PTR_HOST) {
+    if (!host_list_ok(list, n, c->n)) return fail(c, NB_EINVAL);
+    NB_CUDA(c, cudaMemcpyAsync(c->ulist, list, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    *d_list = c->ulist;
+  } else if (ptr_kind == NB_PTR_DEVICE) {
+    NB_CUDA(c, nb_launch_check_list(list, n, c->n, &c->status->flags, c->stream));
+    *d_list = list;
+  } else {
+    return fail(c, NB_EINVAL);
+  }
+  return NB_OK;
+}
+
+// copy a [count][3] AoS array into SoA rows dst[3][stride] at offset first
+int put_vec(nb_ctx* c, const double* src, double* dst, int64_t first, int64_t count, int ptr_kind) {
+  if (!src) {
+    for (int k = 0; k < 3; ++k)
+      NB_CUDA(c, cudaMemsetAsync(dst + k * c->n_pad + first, 0, count * sizeof(double), c->stream));
+    return NB_OK;
+  }
+  const double* d_src = src;
+  if (ptr_kind == NB_PTR_HOST) {
+    NB_CUDA(c, cudaMemcpyAsync(c->part, src, 3 * count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    d_src = c->part;
+  }
+  NB_CUDA(c, nb_launch_aos_to_soa(d_src, dst + first, count, c->n_pad, c->stream));
+  return NB_OK;
+}
+
+int put_scalar(nb_ctx* c, const double* src, double* dst, int64_t first, int64_t count, int ptr_kind) {
+  if (!src) {
+    NB_CUDA(c, cudaMemsetAsync(dst + first, 0, count * sizeof(double), c->stream));
+    return NB_OK;
+  }
+  NB_CUDA(c, cudaMemcpyAsync(dst + first, src, count * sizeof(double),
+                             ptr_kind == NB_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                             c->stream));
+  return NB_OK;
+}
+
+int get_vec(nb_ctx* c, const double* src_soa, int64_t stride, double* dst, int64_t count, int ptr_kind) {
+  if (!dst) return NB_OK;
+  if (ptr_kind == NB_PTR_HOST) {
+    NB_CUDA(c, nb_launch_soa_to_aos(src_soa, stride, c->part, count, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(dst, c->part, 3 * count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    NB_CUDA(c, nb_launch_soa_to_aos(src_soa, stride, dst, count, c->stream));
+  }
+  return NB_OK;
+}
+
+int get_scalar(nb_ctx* c, const double* src, double* dst, int64_t count, int ptr_kind) {
+  if (!dst) return NB_OK;
+  NB_CUDA(c, cudaMemcpyAsync(dst, src, count * sizeof(double),
+                             ptr_kind == NB_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                             c->stream));
+  return NB_OK;
+}
+
+// block selection with the result copied to host: t_next, n
+int select_block(nb_ctx* c, double* t_next, int64_t* n) {
+  NB_CUDA(c, nb_launch_select(c));
+  unsigned char* h = (unsigned char*)c->hpin;
+  NB_CUDA(c, cudaMemcpyAsync(h, c->sel_min + c->sel_ctas, 8, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h + 8, c->sel_cnt + c->sel_ctas, 4, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  unsigned long long bits;
+  int32_t cnt;
+  memcpy(&bits, h, 8);
+  memcpy(&cnt, h + 8, 4);
+  double t;
+  memcpy(&t, &bits, 8);
+  *t_next = t;
+  *n = cnt;
+  return NB_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();  // do not leave the error for a later launch check to see
+    return 0.0f;
+  }
+  return ms;
+}
+
+// one block step after selection (t_next, n known): predict, forces, correct
+int step_after_select(nb_ctx* c, double t, int64_t n) {
+  NB_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  NB_CUDA(c, nb_launch_predict(c, t, false));
+  NB_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  NB_CUDA(c, nb_forces(c, c->act, n));
+  NB_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  NB_CUDA(c, nb_launch_correct(c, c->act, n, t));
+  NB_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  c->interactions += (double)n * (double)c->n;
+  c->pred_valid = false;
+  c->f_valid = false;
+  c->ev_pending = true;
+  c->steps += 1;
+  return NB_OK;
+}
+
+void harvest_timings(nb_ctx* c) {
+  if (!c->ev_pending) return;
+  c->ev_pending = false;
+  c->ms_pred += elapsed(c->ev[0], c->ev[1]);
+  c->ms_force += elapsed(c->ev[1], c->ev[2]);
+  c->ms_corr += elapsed(c->ev[2], c->ev[3]);
+}
+
+int device_status_code(nb_ctx* c, int64_t* underflows) {
+  nb_dev_status st;
+  NB_CUDA(c, cudaMemcpyAsync(c->hpin, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  memcpy(&st, c->hpin, sizeof(st));
+  if (underflows) *underflows = (int64_t)st.dt_underflows;
+  if (st.flags & NB_ST_TIMEOUT) return NB_ETIMEOUT;
+  if (st.flags & NB_ST_NUMERIC) return NB_ENUMERIC;
+  if (st.flags & NB_ST_BADLIST) return NB_EINVAL;
+  return NB_OK;
+}
+
+}  // namespace
+
+// the force dispatcher used by every entry point
+cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
+  const nb_tuning cfg = pick_tuning(c, n);
+  return c->precision == NB_FP64 ? nb_forces_fp64(c, d_list, n, cfg) : nb_forces_mixed(c, d_list, n, cfg);
+}
+
+extern "C" {
+
+void nb_default_params(double* eps, double* eta, double* dt_min, double* dt_max) {
+  if (eps) *eps = kDefaultEps;
+  if (eta) *eta = kDefaultEta;
+  if (dt_min) *dt_min = kDefaultDtMin;
+  if (dt_max) *dt_max = kDefaultDtMax;
+}
+
+const char* nb_version(void) { return "libnbody 0.1 (sm_103a)"; }
+
+const char* nb_strerror(int code) {
+  switch (code) {
+    case NB_OK: return "ok";
+    case NB_EINVAL: return "invalid argument";
+    case NB_ENOMEM: return "out of memory";
+    case NB_ECUDA: return "CUDA runtime error";
+    case NB_ENUMERIC: return "NaN or Inf in a result";
+    case NB_EDTMIN: return "time-step criterion below dt_min";
+    case NB_ETIMEOUT: return "bounded device wait timed out";
+    case NB_ESTATE: return "call out of order";
+    default: return "unknown status code";
+  }
+}
+
+int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda_stream) {
+  if (!out) return NB_EINVAL;
+  *out = nullptr;
+  if (n_max < 1 || n_max > ((int64_t)1 << 30) || (precision != NB_FP64 && precision != NB_MIXED))
+    return NB_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NB_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return NB_ECUDA;
+  nb_ctx* c = (nb_ctx*)calloc(1, sizeof(nb_ctx));
+  if (!c) return NB_ENOMEM;
+  c->device = device;
+  c->precision = precision;
+  c->eps = kDefaultEps;
+  c->eta = kDefaultEta;
+  c->dt_min = kDefaultDtMin;
+  c->dt_max = kDefaultDtMax;
+  c->n_max = n_max;
+  c->n_pad = ((n_max + NB_JPAD - 1) / NB_JPAD) * NB_JPAD;
+  c->sel_ctas = 1024;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  c->sm_count = sms > 0 ? sms : 1;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = true;
+  }
+  const size_t np = (size_t)c->n_pad;
+  c->part_elems = 7 * std::max<int64_t>(c->n_pad, (int64_t)1 << 21);
+#define NB_ALLOC(ptr, cnt) \
+  if (e == cudaSuccess) e = dalloc(&(ptr), (cnt));
+  NB_ALLOC(c->m, np) NB_ALLOC(c->x, 3 * np) NB_ALLOC(c->v, 3 * np) NB_ALLOC(c->a, 3 * np)
+  NB_ALLOC(c->jk, 3 * np) NB_ALLOC(c->pot, np) NB_ALLOC(c->t, np) NB_ALLOC(c->dt, np)
+  NB_ALLOC(c->xp, 3 * np) NB_ALLOC(c->vp, 3 * np) NB_ALLOC(c->jA, np) NB_ALLOC(c->jB, np)
+  NB_ALLOC(c->jC, np) NB_ALLOC(c->F, 7 * np) NB_ALLOC(c->part, (size_t)c->part_elems)
+  NB_ALLOC(c->act, np) NB_ALLOC(c->ident, np) NB_ALLOC(c->ulist, np)
+  NB_ALLOC(c->sel_min, (size_t)c->sel_ctas + 1) NB_ALLOC(c->sel_cnt, (size_t)c->sel_ctas + 1)
+  NB_ALLOC(c->red, 2 * 1024 + 8) NB_ALLOC(c->status, 1)
+#undef NB_ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost(&c->hpin, kPinnedBytes);
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+  if (e == cudaSuccess) {
+    // zero state, padding particles are written by the predictor
+    const size_t bytes[] = {np, 3 * np, 3 * np, 3 * np, 3 * np, np, np, np};
+    double* ptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt};
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i)
+      e = cudaMemsetAsync(ptrs[i], 0, bytes[i] * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(nb_dev_status), c->stream);
+    if (e == cudaSuccess) e = nb_launch_fill_ident(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (e != cudaSuccess) {
+    const int code = e == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA;
+    free_ctx(c);
+    cudaGetLastError();
+    return code;
+  }
+  *out = c;
+  return NB_OK;
+}
+
+void nb_destroy(nb_ctx* c) {
+  if (!c) return;
+  select_device(c);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  nb_ensemble_free(c);
+  free_ctx(c);
+}
+
+int nb_set_params(nb_ctx* c, double eps, double eta, double dt_min, double dt_max) {
+  if (!c) return NB_EINVAL;
+  if (!(eps >= 0.0) || !isfinite(eps) || !(eta > 0.0) || !isfinite(eta) || !is_pow2(dt_min) ||
+      !is_pow2(dt_max) || dt_min > dt_max)
+    return fail(c, NB_EINVAL);
+  c->eps = eps;
+  c->eta = eta;
+  c->dt_min = dt_min;
+  c->dt_max = dt_max;
+  return NB_OK;
+}
+
+int nb_set_precision(nb_ctx* c, int precision) {
+  if (!c) return NB_EINVAL;
+  if (precision != NB_FP64 && precision != NB_MIXED) return fail(c, NB_EINVAL);
+  if (precision != c->precision) c->pred_valid = false;
+  c->precision = precision;
+  return NB_OK;
+}
+
+int nb_set_j_particles(nb_ctx* c, int64_t first, int64_t count, const double* m, const double* x,
+                       const double* v, const double* a, const double* jerk, const double* t,
+                       const double* dt, int ptr_kind) {
+  NB_ENTER(c);
+  if (count < 0 || first < 0 || first + count > c->n_max || !m || !x || !v ||
+      (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (count == 0) return NB_OK;
+  if (ptr_kind == NB_PTR_HOST) {
+    const double* arrs[] = {m, x, v, a, jerk, t, dt};
+    const int64_t lens[] = {count, 3 * count, 3 * count, 3 * count, 3 * count, count, count};
+    for (int q = 0; q < 7; ++q) {
+      if (!arrs[q]) continue;
+      for (int64_t i = 0; i < lens[q]; ++i)
+        if (!isfinite(arrs[q][i])) return fail(c, NB_EINVAL);
+    }
+  }
+  int r;
+  if ((r = put_scalar(c, m, c->m, first, count, ptr_kind))) return r;
+  if ((r = put_vec(c, x, c->x, first, count, ptr_kind))) return r;
+  if ((r = put_vec(c, v, c->v, first, count, ptr_kind))) return r;
+  if ((r = put_vec(c, a, c->a, first, count, ptr_kind))) return r;
+  if ((r = put_vec(c, jerk, c->jk, first, count, ptr_kind))) return r;
+  if ((r = put_scalar(c, t, c->t, first, count, ptr_kind))) return r;
+  if ((r = put_scalar(c, dt, c->dt, first, count, ptr_kind))) return r;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (first + count > c->n) c->n = first + count;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}
+
+int nb_set_n(nb_ctx* c, int64_t n) {
+  if (!c) return NB_EINVAL;
+  if (n < 0 || n > c->n_max) return fail(c, NB_EINVAL);
+  c->n = n;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}
+
+int nb_get_n(nb_ctx* c, int64_t* n) {
+  if (!c || !n) return NB_EINVAL;
+  *n = c->n;
+  return NB_OK;
+}
+
+int nb_get_particles(nb_ctx* c, int64_t first, int64_t count, double* m, double* x, double* v,
+                     double* a, double* jerk, double* pot, double* t, double* dt, int ptr_kind) {
+  NB_ENTER(c);
+  if (count < 0 || first < 0 || first + count > c->n ||
+      (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (count == 0) return NB_OK;
+  int r;
+  // vectors pass through the staging area one at a time on the stream
+  const double* soa[] = {c->x, c->v, c->a, c->jk};
+  double* dst[] = {x, v, a, jerk};
+  for (int q = 0; q < 4; ++q) {
+    if (!dst[q]) continue;
+    if ((r = get_vec(c, soa[q] + first, c->n_pad, dst[q], count, ptr_kind))) return r;
+    if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  if ((r = get_scalar(c, c->m + first, m, count, ptr_kind))) return r;
+  if ((r = get_scalar(c, c->pot + first, pot, count, ptr_kind))) return r;
+  if ((r = get_scalar(c, c->t + first, t, count, ptr_kind))) return r;
+  if ((r = get_scalar(c, c->dt + first, dt, count, ptr_kind))) return r;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
+int nb_next_block(nb_ctx* c, double* t_next, int32_t* active_idx, int64_t* n_active) {
+  NB_SINGLE(c);
+  if (!t_next || !n_active) return fail(c, NB_EINVAL);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  int r = select_block(c, t_next, n_active);
+  if (r) return r;
+  if (active_idx && *n_active > 0) {
+    NB_CUDA(c, cudaMemcpyAsync(active_idx, c->act, *n_active * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return NB_OK;
+}
+
+int nb_predict(nb_ctx* c, double t) {
+  NB_SINGLE(c);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  if (!isfinite(t)) return fail(c, NB_EINVAL);
+  NB_CUDA(c, nb_launch_predict(c, t, false));
+  c->t_pred = t;
+  c->pred_valid = true;
+  return NB_OK;
+}
+
+int nb_compute_forces(nb_ctx* c, const int32_t* i_idx, int64_t n, double* acc, double* jerk, double* pot,
+                      int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n || (n > 0 && !i_idx)) return fail(c, NB_EINVAL);
+  if (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE) return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  const int32_t* d_list = nullptr;
+  int r = stage_list(c, i_idx, n, ptr_kind, &d_list);
+  if (r) return r;
+  NB_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
+  NB_CUDA(c, nb_forces(c, d_list, n));
+  NB_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
+  c->f_n = n;
+  c->f_valid = true;
+  c->f_list = d_list;
+  c->interactions += (double)n * (double)c->n;
+  for (int q = 0; q < 2; ++q) {
+    double* dst = q == 0 ? acc : jerk;
+    if (!dst) continue;
+    if ((r = get_vec(c, c->F + 3 * q * c->n_pad, c->n_pad, dst, n, ptr_kind))) return r;
+    if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  if ((r = get_scalar(c, c->F + 6 * c->n_pad, pot, n, ptr_kind))) return r;
+  if (ptr_kind == NB_PTR_HOST) {
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->ms_force += elapsed(c->ev[4], c->ev[5]);
+  }
+  return NB_OK;
+}
+
+int nb_correct(nb_ctx* c, const int32_t* i_idx, int64_t n, double t, int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n || (n > 0 && !i_idx) || !isfinite(t)) return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  if (!c->f_valid || c->f_n != n || !c->pred_valid) return fail(c, NB_ESTATE);
+  const int32_t* d_list = nullptr;
+  int r = stage_list(c, i_idx, n, ptr_kind, &d_list);
+  if (r) return r;
+  NB_CUDA(c, nb_launch_correct(c, d_list, n, t));
+  c->f_valid = false;
+  c->pred_valid = false;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
+int nb_initial_forces_and_dt(nb_ctx* c) {
+  NB_ENTER(c);
+  if (c->n_clusters > 0) {
+    const int r = nb_ensemble_initial_forces_and_dt(c);
+    return r == NB_OK ? r : fail(c, r);
+  }
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  NB_CUDA(c, nb_launch_predict(c, 0.0, true));
+  NB_CUDA(c, nb_forces(c, c->ident, c->n));
+  NB_CUDA(c, nb_launch_initial_dt(c));
+  c->interactions += (double)c->n * (double)c->n;
+  c->pred_valid = false;
+  c->f_valid = false;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return device_status_code(c, nullptr) == NB_ENUMERIC ? fail(c, NB_ENUMERIC) : NB_OK;
+}
+
+int nb_step(nb_ctx* c, double* t_out, int64_t* n_out) {
+  NB_SINGLE(c);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  double t;
+  int64_t n;
+  int r = select_block(c, &t, &n);
+  if (r) return r;
+  if (!isfinite(t) || n <= 0) return fail(c, NB_ENUMERIC);
+  if ((r = step_after_select(c, t, n))) return r;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  harvest_timings(c);
+  if (t_out) *t_out = t;
+  if (n_out) *n_out = n;
+  return NB_OK;
+}
+
+static int integrate_host_loop(nb_ctx* c, double t_end) {
+  for (;;) {
+    double t;
+    int64_t n;
+    int r = select_block(c, &t, &n);
+    if (r) return r;
+    harvest_timings(c);
+    if (!isfinite(t) || n <= 0) return fail(c, NB_ENUMERIC);
+    if (t > t_end) break;
+    if ((r = step_after_select(c, t, n))) return r;
+  }
+  return NB_OK;
+}
+
+}  // extern "C"
+int nb_integrate_graph(nb_ctx* c, double t_end);
+extern "C" {
+
+int nb_integrate(nb_ctx* c, double t_end, int use_graph) {
+  NB_SINGLE(c);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  if (!(t_end > 0.0) || !isfinite(t_end) || fmod(t_end, c->dt_max) != 0.0) return fail(c, NB_EINVAL);
+  int r = use_graph ? nb_integrate_graph(c, t_end) : integrate_host_loop(c, t_end);
+  if (r) return r;
+  r = device_status_code(c, nullptr);
+  if (r == NB_ENUMERIC || r == NB_ETIMEOUT) return fail(c, r);
+  return NB_OK;
+}
+
+int nb_energy(nb_ctx* c, double* ekin, double* epot) {
+  NB_SINGLE(c);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  NB_CUDA(c, nb_launch_predict(c, 0.0, true));
+  NB_CUDA(c, nb_forces(c, c->ident, c->n));
+  double* d_out = c->red + 2 * 1024;
+  NB_CUDA(c, nb_launch_energy(c, c->F + 6 * c->n_pad, d_out));
+  NB_CUDA(c, cudaMemcpyAsync(c->hpin, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  double h[2];
+  memcpy(h, c->hpin, sizeof(h));
+  if (ekin) *ekin = h[0];
+  if (epot) *epot = h[1];
+  c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}
+
+int nb_get_timings(nb_ctx* c, double* ms_pred, double* ms_force, double* ms_corr, double* interactions,
+                   int reset) {
+  if (!c) return NB_EINVAL;
+  if (ms_pred) *ms_pred = c->ms_pred;
+  if (ms_force) *ms_force = c->ms_force;
+  if (ms_corr) *ms_corr = c->ms_corr;
+  if (interactions) *interactions = c->interactions;
+  if (reset) c->ms_pred = c->ms_force = c->ms_corr = c->interactions = 0.0;
+  return NB_OK;
+}
+
+int nb_get_counters(nb_ctx* c, int64_t* kernel_launches, int64_t* block_steps) {
+  if (!c) return NB_EINVAL;
+  if (kernel_launches) *kernel_launches = c->launches;
+  if (block_steps) *block_steps = c->steps;
+  return NB_OK;
+}
+
+int nb_check_device_status(nb_ctx* c, int64_t* dt_underflows) {
+  NB_ENTER(c);
+  return device_status_code(c, dt_underflows);
+}
+
+int nb_last_error(nb_ctx* c) { return c ? c->last_error : NB_EINVAL; }
+
+void nb_clear_error(nb_ctx* c) {
+  if (!c) return;
+  c->last_error = NB_OK;
+  if (select_device(c) == NB_OK) {
+    cudaMemsetAsync(c->status, 0, sizeof(nb_dev_status), c->stream);
+    cudaStreamSynchronize(c->stream);
+  }
+}
+
+int nb_set_tuning(nb_ctx* c, int i_per_thread, int threads, int j_tile, int n_split) {
+  if (!c) return NB_EINVAL;
+  nb_tuning t{i_per_thread, threads, j_tile, n_split};
+  if (i_per_thread || threads || j_tile || n_split) {
+    nb_tuning d = nb_default_tuning(c->precision);
+    nb_tuning full{i_per_thread ? i_per_thread : d.ipt, threads ? threads : d.threads,
+                   j_tile ? j_tile : d.jtile, n_split};
+    if (!nb_tuning_supported(c->precision, full)) return fail(c, NB_EINVAL);
+  }
+  c->tune_override = t;
+  return NB_OK;
+}
+
+int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split) {
+  NB_SINGLE(c);
+  if (n < 1 || n > c->n) return fail(c, NB_EINVAL);
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  static const int thr_list[] = {64, 128, 256};
+  static const int ipt_mixed[] = {1, 2, 4};
+  static const int jt_mixed[] = {64, 128, 256};
+  static const int jt_fp64[] = {32, 64, 128};
+  nb_tuning best{0, 0, 0, 0};
+  float best_ms = 1e30f;
+  const nb_tuning saved = c->tune_override;
+  for (int ti = 0; ti < 3; ++ti) {
+    for (int ii = 0; ii < (c->precision == NB_MIXED ? 3 : 1); ++ii) {
+      for (int ji = 0; ji < 3; ++ji) {
+        nb_tuning cfg{c->precision == NB_MIXED ? ipt_mixed[ii] : 1, thr_list[ti],
+                      c->precision == NB_MIXED ? jt_mixed[ji] : jt_fp64[ji], 0};
+        if (!nb_tuning_supported(c->precision, cfg)) continue;
+        cfg.nsplit = nb_auto_split(c, n, cfg);
+        const int splits[] = {cfg.nsplit, std::max(1, cfg.nsplit / 2), cfg.nsplit * 2};
+        for (int si = 0; si < 3; ++si) {
+          if (si > 0 && splits[si] == cfg.nsplit) continue;
+          nb_tuning t = cfg;
+          t.nsplit = splits[si];
+          c->tune_override = t;
+          NB_CUDA(c, nb_forces(c, c->ident, n));  // warm-up
+          NB_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
+          NB_CUDA(c, nb_forces(c, c->ident, n));
+          NB_CUDA(c, cudaEventRecord(c->ev[7], c->stream));
+          NB_CUDA(c, cudaStreamSynchronize(c->stream));
+          float ms = elapsed(c->ev[6], c->ev[7]);
+          if (ms < 5.0f) {  // short launches: average a few more
+            const int reps = 5;
+            NB_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
+            for (int r = 0; r < reps; ++r) NB_CUDA(c, nb_forces(c, c->ident, n));
+            NB_CUDA(c, cudaEventRecord(c->ev[7], c->stream));
+            NB_CUDA(c, cudaStreamSynchronize(c->stream));
+            ms = elapsed(c->ev[6], c->ev[7]) / reps;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+          }
+        }
+      }
+    }
+  }
+  c->tune_override = saved;
+  c->f_valid = false;
+  if (best.threads == 0) return fail(c, NB_ECUDA);
+  // table entry for blocks within a factor sqrt(2) of n (replaces an overlapping one)
+  const int64_t lo = (int64_t)(n / 1.41421356), hi = (int64_t)(n * 1.41421356) + 1;
+  int slot = -1;
+  for (int i = 0; i < c->tune_count; ++i)
+    if (c->tune_table[i].n_lo < hi && lo < c->tune_table[i].n_hi) slot = i;
+  if (slot < 0) slot = c->tune_count < 16 ? c->tune_count++ : 15;
+  c->tune_table[slot] = nb_tune_entry{lo, hi, best};
+  if (i_per_thread) *i_per_thread = best.ipt;
+  if (threads) *threads = best.threads;
+  if (j_tile) *j_tile = best.jtile;
+  if (n_split) *n_split = best.nsplit;
+  return NB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,970 @@
+// ensemble.cu -- device-driven block steps for one or many independent
+// systems ("clusters"): the CUDA-graph integration loop of a single system
+// (nb_integrate with use_graph) and the batched ensemble (nb_ensemble_*).
+//
+// Every kernel reads the block state from device memory, so a whole block
+// step -- selection (Sec. 4.1 step 2), prediction (3), forces (4), correction
+// (5) -- needs no host round trip, and the loop of steps 2-6 runs as one CUDA
+// graph whose body sits in a device-side while node.  All clusters advance
+// together: each body iteration takes the next block step of every cluster
+// that has not reached t_end (each at its own block time), and the force work
+// of all clusters is flattened into one list of (cluster, i-tile, j-split)
+// items that a persistent kernel spreads over all SMs.  Clusters of very
+// different size and block size therefore share the GPU without a per-cluster
+// critical path.
+//
+// Cluster c owns particles [off[c], off[c+1]) of the j-store and the same
+// slots of the active list and of the force results.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "force_common.cuh"
+
+namespace {
+
+constexpr int kSelChunk = 2048;   // particles per selection chunk (chunks never straddle clusters)
+constexpr int kMixNT = 128, kMixIPT = 2, kMixJT = 128;   // batched mixed item shape
+constexpr int kF64NT = 128, kF64JT = 64;                 // batched FP64 item shape
+constexpr int64_t kMaxIters = 50000000;                  // hard cap on loop iterations
+
+struct BParams {
+  double t_end, eta, dt_min, dt_max;
+  int64_t max_iters;
+};
+
+struct Batch {
+  int32_t C = 0;
+  int64_t N = 0;
+  int32_t nchunks = 0;
+  // device
+  int64_t* off = nullptr;          // [C+1]
+  float* eps2f = nullptr;          // [C]
+  double* eps2d = nullptr;         // [C]
+  int32_t* cid = nullptr;          // [n_pad] cluster of a particle / slot
+  int32_t* ch_cluster = nullptr;   // [nchunks]
+  int64_t* ch_lo = nullptr;        // [nchunks]
+  int64_t* ch_hi = nullptr;        // [nchunks]
+  int32_t* cl_ch0 = nullptr;       // [C+1] first chunk of each cluster
+  unsigned long long* ch_min = nullptr;  // [nchunks]
+  int32_t* ch_cnt = nullptr;       // [nchunks]
+  double* tnext = nullptr;         // [C]
+  int32_t* nact = nullptr;         // [C]
+  int32_t* itiles = nullptr;       // [C]
+  int32_t* nsplit = nullptr;       // [C]
+  int64_t* jps = nullptr;          // [C] j per split
+  int64_t* item_off = nullptr;     // [C+1]
+  int64_t* part_off = nullptr;     // [C]
+  int64_t* pstride = nullptr;      // [C]
+  int64_t* ctrl = nullptr;         // [4]: any active, iterations, interactions (as int64), spare
+  BParams* prm = nullptr;
+  double* esum = nullptr;          // [2C] per-cluster energies
+  // host
+  std::vector<int64_t> h_off;
+  int grid_mixed = 0, grid_fp64 = 0;
+  cudaGraphExec_t exec = nullptr;
+  int exec_precision = -1;
+  nb_ctx* child = nullptr;         // per-cluster reference path
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// ---------------------------------------------------------------------------
+// selection (Sec. 4.1 step 2) per cluster: t_next[c] = min (t_i + dt_i) over
+// the cluster; active slots off[c] + k, k < n_c, ascending index.
+// ---------------------------------------------------------------------------
+__global__ void b_sel_min(const int64_t* __restrict__ lo, const int64_t* __restrict__ hi,
+                          const double* __restrict__ ti, const double* __restrict__ dt,
+                          unsigned long long* __restrict__ ch_min) {
+  const int j = blockIdx.x;
+  unsigned long long best = 0x7FF0000000000000ULL;
+  for (int64_t i = lo[j] + threadIdx.x; i < hi[j]; i += blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(ti[i] + dt[i]);
+    best = b < best ? b : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+    best = w < best ? w : best;
+  }
+  __shared__ unsigned long long sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sm[w] < best ? sm[w] : best;
+    best = sm[0] < best ? sm[0] : best;
+    ch_min[j] = best;
+  }
+}
+
+__device__ __forceinline__ double cluster_tmin(const unsigned long long* ch_min, int a, int b) {
+  unsigned long long best = 0x7FF0000000000000ULL;
+  for (int q = a; q < b; ++q) best = ch_min[q] < best ? ch_min[q] : best;
+  return __longlong_as_double((long long)best);
+}
+
+__global__ void b_sel_count(const int32_t* __restrict__ ch_cluster, const int64_t* __restrict__ lo,
+                            const int64_t* __restrict__ hi, const int32_t* __restrict__ cl_ch0,
+                            const unsigned long long* __restrict__ ch_min, const double* __restrict__ ti,
+                            const double* __restrict__ dt, double* __restrict__ tnext,
+                            int32_t* __restrict__ ch_cnt) {
+  const int j = blockIdx.x;
+  const int c = ch_cluster[j];
+  __shared__ double tn;
+  if (threadIdx.x == 0) {
+    tn = cluster_tmin(ch_min, cl_ch0[c], cl_ch0[c + 1]);
+    if (j == cl_ch0[c]) tnext[c] = tn;
+  }
+  __syncthreads();
+  int cnt = 0;
+  for (int64_t i = lo[j] + threadIdx.x; i < hi[j]; i += blockDim.x) cnt += (ti[i] + dt[i] == tn) ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __shared__ int sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+    ch_cnt[j] = s;
+  }
+}
+
+__global__ void b_sel_write(const int32_t* __restrict__ ch_cluster, const int64_t* __restrict__ lo,
+                            const int64_t* __restrict__ hi, const int32_t* __restrict__ cl_ch0,
+                            const int32_t* __restrict__ ch_cnt, const int64_t* __restrict__ off,
+                            const double* __restrict__ ti, const double* __restrict__ dt,
+                            const double* __restrict__ tnext, const BParams* __restrict__ prm,
+                            int32_t* __restrict__ act, int32_t* __restrict__ nact) {
+  const int j = blockIdx.x;
+  const int c = ch_cluster[j];
+  const double tn = tnext[c];
+  __shared__ int base_s;
+  if (threadIdx.x == 0) {
+    int b = 0, tot = 0;
+    for (int q = cl_ch0[c]; q < cl_ch0[c + 1]; ++q) {
+      if (q < j) b += ch_cnt[q];
+      tot += ch_cnt[q];
+    }
+    base_s = b;
+    if (j == cl_ch0[c]) nact[c] = (tn <= prm->t_end) ? tot : 0;
+  }
+  __syncthreads();
+  int base = (int)off[c] + base_s;
+  __shared__ int wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t seg = lo[j]; seg < hi[j]; seg += blockDim.x) {
+    const int64_t i = seg + threadIdx.x;
+    const bool f = (i < hi[j]) && (ti[i] + dt[i] == tn);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int pre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int wpre = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int cc = wsum[w];
+      if (w < wid) wpre += cc;
+      tot += cc;
+    }
+    if (f) act[base + wpre + pre] = (int32_t)i;
+    base += tot;
+    __syncthreads();
+  }
+}
+
+// all particles active at their own time (initial forces / energies)
+__global__ void b_all_active(int32_t C, const int64_t* __restrict__ off, int64_t N, int32_t* __restrict__ act,
+                             int32_t* __restrict__ nact, double* __restrict__ tnext) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    act[i] = (int32_t)i;
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      nact[c] = (int32_t)(off[c + 1] - off[c]);
+      tnext[c] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plan: per cluster i-tiles and j-splits, flattened item offsets, partial-sum
+// offsets; loop control (any cluster active, iteration cap).  One CTA.
+// The j-split length L is common to all clusters and chosen so that the whole
+// batch yields about 4 items per resident CTA.
+// ---------------------------------------------------------------------------
+__device__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total) {
+  // Hillis-Steele over blockDim.x <= 1024 entries
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int64_t add = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += add;
+    __syncthreads();
+  }
+  const int64_t incl = sh[t];
+  *total = sh[blockDim.x - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
+                       int per_cta, int jtile, int64_t target_items, int64_t part_cap,
+                       int32_t* __restrict__ itiles, int32_t* __restrict__ nsplit, int64_t* __restrict__ jps,
+                       int64_t* __restrict__ item_off, int64_t* __restrict__ part_off,
+                       int64_t* __restrict__ pstride, int64_t* __restrict__ ctrl,
+                       const BParams* __restrict__ prm, nb_dev_status* __restrict__ st,
+                       cudaGraphConditionalHandle handle, int use_handle) {
+  __shared__ int64_t sh[1024];
+  __shared__ int64_t s_L;
+  __shared__ int s_retry;
+  const int t = threadIdx.x;
+  // pass 1: total slot-pair work and activity
+  int64_t w = 0, anyact = 0, inter = 0;
+  for (int c = t; c < C; c += blockDim.x) {
+    const int64_t n = nact[c];
+    const int64_t Nc = off[c + 1] - off[c];
+    const int64_t it = (n + per_cta - 1) / per_cta;
+    w += it * per_cta * Nc;
+    anyact += n > 0;
+    inter += n * Nc;
+  }
+  int64_t tot_w, tot_a, tot_i;
+  block_excl_scan(w, sh, &tot_w);
+  block_excl_scan(anyact, sh, &tot_a);
+  block_excl_scan(inter, sh, &tot_i);
+  if (t == 0) {
+    int64_t L = tot_w / ((int64_t)per_cta * (target_items > 0 ? target_items : 1));
+    L = ((L + jtile - 1) / jtile) * jtile;
+    s_L = L < jtile ? jtile : L;
+  }
+  __syncthreads();
+  for (int attempt = 0; attempt < 40; ++attempt) {
+    const int64_t L = s_L;
+    int64_t item_carry = 0, part_carry = 0;
+    for (int c0 = 0; c0 < C; c0 += blockDim.x) {
+      const int c = c0 + t;
+      int64_t items = 0, psz = 0;
+      int32_t it = 0, ns = 1;
+      int64_t jp = 0, ps = 0;
+      if (c < C) {
+        const int64_t n = nact[c];
+        const int64_t Nc = off[c + 1] - off[c];
+        it = (int32_t)((n + per_cta - 1) / per_cta);
+        const int64_t tiles = (Nc + jtile - 1) / jtile;
+        int64_t s = (Nc + L - 1) / L;
+        if (s > tiles) s = tiles;
+        if (s < 1) s = 1;
+        const int64_t tps = (tiles + s - 1) / s;
+        s = (tiles + tps - 1) / tps;
+        ns = (int32_t)s;
+        jp = tps * jtile;
+        ps = ((n + 31) / 32) * 32;
+        items = (int64_t)it * s;
+        psz = s > 1 ? 7 * s * ps : 0;
+      }
+      int64_t tot_items, tot_part;
+      const int64_t ex_items = block_excl_scan(items, sh, &tot_items);
+      const int64_t ex_part = block_excl_scan(psz, sh, &tot_part);
+      if (c < C) {
+        itiles[c] = it;
+        nsplit[c] = ns;
+        jps[c] = jp;
+        pstride[c] = ps;
+        item_off[c] = item_carry + ex_items;
+        part_off[c] = part_carry + ex_part;
+      }
+      item_carry += tot_items;
+      part_carry += tot_part;
+    }
+    if (t == 0) {
+      item_off[C] = item_carry;
+      s_retry = part_carry > part_cap;
+      if (s_retry) s_L = s_L * 2;
+    }
+    __syncthreads();
+    if (!s_retry) break;
+  }
+  if (t == 0) {
+    int64_t iters = ctrl[1] + 1;
+    ctrl[1] = iters;
+    ctrl[2] += tot_i;
+    int go = tot_a > 0;
+    if (go && iters > prm->max_iters) {
+      atomicOr(&st->flags, NB_ST_TIMEOUT);
+      go = 0;
+    }
+    if (s_retry) {  // partial sums do not fit: stop with an error instead of overflowing
+      atomicOr(&st->flags, NB_ST_TIMEOUT);
+      go = 0;
+      item_off[C] = 0;
+    }
+    ctrl[0] = go;
+    if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// predictor per cluster (Sec. 4.1 step 3): particles of active clusters to
+// their cluster's block time (own_time: h = 0).
+// ---------------------------------------------------------------------------
+__global__ void b_predict(int64_t N, int64_t n_pad, const int32_t* __restrict__ cid,
+                          const int32_t* __restrict__ nact, const double* __restrict__ tnext, int own_time,
+                          const double* __restrict__ m, const double* __restrict__ x,
+                          const double* __restrict__ v, const double* __restrict__ a,
+                          const double* __restrict__ jk, const double* __restrict__ ti,
+                          double* __restrict__ xp, double* __restrict__ vp, float4* __restrict__ jA,
+                          float4* __restrict__ jB, float2* __restrict__ jC, int write_fp64, int write_mixed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cid[i];
+    if (nact[c] == 0) continue;
+    const double h = own_time ? 0.0 : tnext[c] - ti[i];
+    double px[3], pv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t q = k * n_pad + i;
+      const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
+      px[k] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
+      pv[k] = vv + h * (av + h * (0.5 * jv));
+    }
+    if (write_fp64) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        xp[k * n_pad + i] = px[k];
+        vp[k * n_pad + i] = pv[k];
+      }
+    }
+    if (write_mixed) {
+      float hi[3], lo[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        hi[k] = __double2float_rn(px[k]);
+        lo[k] = __double2float_rn(px[k] - (double)hi[k]);
+      }
+      jA[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m[i]));
+      jB[i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
+      jC[i] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forces (Sec. 4.1 step 4): persistent CTAs over the flattened item list
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_cluster(const int64_t* __restrict__ item_off, int C, int64_t item) {
+  int lo = 0, hi = C;  // item_off[lo] <= item < item_off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (item_off[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int NT, int IPT, int JT>
+__global__ void __launch_bounds__(NT) b_force_mixed(
+    int32_t C, const int64_t* __restrict__ off, const float* __restrict__ eps2f, int64_t n_pad,
+    const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
+    const int32_t* __restrict__ act, const int32_t* __restrict__ nact, const int32_t* __restrict__ itiles,
+    const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
+    const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
+    int64_t fstride, double* __restrict__ part) {
+  __shared__ __align__(16) nbk::MixedSmem<JT> sm;
+  const int64_t total = item_off[C];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_cluster(item_off, C, item);
+    const int64_t local = item - item_off[c];
+    const int it = itiles[c];
+    const int64_t itile = local % it, split = local / it;
+    const int64_t jlo = off[c] + split * jps[c];
+    const int64_t jhi = min(jlo + jps[c], off[c + 1]);
+    const bool fin = nsplit[c] == 1;
+    double* out = fin ? F + off[c] : part + part_off[c] + split * 7 * pstride[c];
+    nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_pad, act + off[c], nact[c], itile * (NT * IPT),
+                                 eps2f[c], out, fin ? fstride : pstride[c], fin);
+  }
+}
+
+template <int NT, int JT>
+__global__ void __launch_bounds__(NT) b_force_fp64(
+    int32_t C, const int64_t* __restrict__ off, const double* __restrict__ eps2d, int64_t n_pad,
+    const double* __restrict__ xp, const double* __restrict__ vp, const double* __restrict__ m,
+    const int32_t* __restrict__ act, const int32_t* __restrict__ nact, const int32_t* __restrict__ itiles,
+    const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
+    const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
+    int64_t fstride, double* __restrict__ part) {
+  __shared__ nbk::Fp64Smem<JT> sm;
+  const int64_t total = item_off[C];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_cluster(item_off, C, item);
+    const int64_t local = item - item_off[c];
+    const int it = itiles[c];
+    const int64_t itile = local % it, split = local / it;
+    const int64_t jlo = off[c] + split * jps[c];
+    const int64_t jhi = min(jlo + jps[c], off[c + 1]);
+    const bool fin = nsplit[c] == 1;
+    double* out = fin ? F + off[c] : part + part_off[c] + split * 7 * pstride[c];
+    nbk::fp64_item<NT, JT>(sm, xp, vp, m, n_pad, jlo, jhi, act + off[c], nact[c], itile * NT, eps2d[c], out,
+                           fin ? fstride : pstride[c], fin);
+  }
+}
+
+// split-j reduction per cluster, fixed order over splits
+__global__ void b_reduce(int64_t N, const int32_t* __restrict__ cid, const int64_t* __restrict__ off,
+                         const int32_t* __restrict__ nact, const int32_t* __restrict__ nsplit,
+                         const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride,
+                         const double* __restrict__ part, double* __restrict__ F, int64_t fstride) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cid[s];
+    const int64_t k = s - off[c];
+    const int S = nsplit[c];
+    if (k >= nact[c] || S <= 1) continue;
+    const double* p = part + part_off[c];
+    const int64_t ps = pstride[c];
+#pragma unroll
+    for (int r = 0; r < 7; ++r) {
+      double acc = 0.0;
+      for (int q = 0; q < S; ++q) acc += p[((int64_t)q * 7 + r) * ps + k];
+      F[r * fstride + s] = r == 6 ? -acc : acc;
+    }
+  }
+}
+
+__device__ __forceinline__ double pow2_floor_b(double x) {
+  if (!(x > 0.0)) return 0.0;
+  if (isinf(x)) return x;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b >> 52) == 0) return 0.0;
+  return __longlong_as_double((long long)(b & 0xFFF0000000000000ULL));
+}
+
+// corrector + block-step rule (Sec. 4.1 step 5), per slot of active clusters
+__global__ void b_correct(int64_t N, int64_t n_pad, const int32_t* __restrict__ cid,
+                          const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
+                          const double* __restrict__ tnext, const int32_t* __restrict__ act,
+                          const double* __restrict__ F, int64_t fstride, const BParams* __restrict__ prm,
+                          double* __restrict__ x, double* __restrict__ v, double* __restrict__ a,
+                          double* __restrict__ jk, double* __restrict__ pot, double* __restrict__ ti,
+                          double* __restrict__ dt, const double* __restrict__ xp,
+                          const double* __restrict__ vp, nb_dev_status* __restrict__ st) {
+  const double eta = prm->eta, dt_min = prm->dt_min, dt_max = prm->dt_max;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cid[s];
+    if (s - off[c] >= nact[c]) continue;
+    int64_t i = act[s];
+    i = i < 0 ? 0 : (i >= n_pad ? n_pad - 1 : i);
+    const double t = tnext[c];
+    const double h = t - ti[i];
+    const double ih = 1.0 / h;
+    const double ih2 = ih * ih, ih3 = ih2 * ih;
+    const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+    double na2 = 0, nj2 = 0, n22 = 0, n32 = 0;
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int64_t q = r * n_pad + i;
+      const double a0 = a[q], j0 = jk[q];
+      const double a1 = F[r * fstride + s], j1 = F[(3 + r) * fstride + s];
+      const double da = a0 - a1;
+      const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
+      const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
+      const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
+      const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+      const double a2e = a2 + a3 * h;
+      x[q] = x1;
+      v[q] = v1;
+      a[q] = a1;
+      jk[q] = j1;
+      na2 += a1 * a1;
+      nj2 += j1 * j1;
+      n22 += a2e * a2e;
+      n32 += a3 * a3;
+      finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
+    }
+    const double p1 = F[6 * fstride + s];
+    pot[i] = p1;
+    const double na = sqrt(na2), nj = sqrt(nj2), n2 = sqrt(n22), n3 = sqrt(n32);
+    const double num = na * n2 + nj * nj;
+    const double den = nj * n3 + n2 * n2;
+    const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
+    if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
+    const double dt_old = dt[i];
+    double cnew = pow2_floor_b(crit);
+    cnew = cnew > dt_max ? dt_max : (cnew < dt_min ? dt_min : cnew);
+    double dnew;
+    if (cnew < dt_old) {
+      dnew = cnew;
+    } else {
+      const double two = 2.0 * dt_old;
+      const double qq = t / two;
+      dnew = (cnew >= two && two <= dt_max && qq == floor(qq)) ? two : dt_old;
+    }
+    if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
+    ti[i] = t;
+    dt[i] = dnew;
+  }
+}
+
+// initial steps for every particle of every cluster (Sec. 4.1 step 1)
+__global__ void b_initial_dt(int64_t N, int64_t n_pad, const double* __restrict__ F, int64_t fstride,
+                             const BParams* __restrict__ prm, double* __restrict__ a, double* __restrict__ jk,
+                             double* __restrict__ pot, double* __restrict__ ti, double* __restrict__ dt,
+                             nb_dev_status* __restrict__ st) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double na2 = 0, nj2 = 0;
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double av = F[r * fstride + i], jv = F[(3 + r) * fstride + i];
+      a[r * n_pad + i] = av;
+      jk[r * n_pad + i] = jv;
+      na2 += av * av;
+      nj2 += jv * jv;
+      finite = finite && isfinite(av) && isfinite(jv);
+    }
+    pot[i] = F[6 * fstride + i];
+    const double nj = sqrt(nj2);
+    const double d = (nj > 0.0) ? prm->eta * sqrt(na2) / nj : (double)INFINITY;
+    double cnew = pow2_floor_b(d);
+    cnew = cnew > prm->dt_max ? prm->dt_max : (cnew < prm->dt_min ? prm->dt_min : cnew);
+    dt[i] = cnew;
+    ti[i] = 0.0;
+    if (!finite) atomicOr(&st->flags, NB_ST_NUMERIC);
+  }
+}
+
+// per-cluster energies: K = sum m v^2/2, W = sum m pot/2 (fixed order per CTA)
+__global__ void b_energy(const int64_t* __restrict__ off, int64_t n_pad, const double* __restrict__ m,
+                         const double* __restrict__ v, const double* __restrict__ F, int64_t fstride,
+                         double* __restrict__ out) {
+  const int c = blockIdx.x;
+  double k = 0.0, w = 0.0;
+  for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x) {
+    const double v0 = v[i], v1 = v[n_pad + i], v2 = v[2 * n_pad + i];
+    k += 0.5 * m[i] * (v0 * v0 + v1 * v1 + v2 * v2);
+    w += 0.5 * m[i] * F[6 * fstride + i];
+  }
+  __shared__ double sk[256], sw[256];
+  sk[threadIdx.x] = k;
+  sw[threadIdx.x] = w;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sk[threadIdx.x] += sk[threadIdx.x + s];
+      sw[threadIdx.x] += sw[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * c] = sk[0];
+    out[2 * c + 1] = sw[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+Batch* batch_of(nb_ctx* c) { return (Batch*)c->ens; }
+
+int grid_for(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+void batch_free(Batch* b) {
+  if (!b) return;
+  void* p[] = {b->off, b->eps2f, b->eps2d, b->cid, b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min,
+               b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
+               b->ctrl, b->prm, b->esum};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->child) nb_destroy(b->child);
+  delete b;
+}
+
+__global__ void fill_cid(int64_t N, const int64_t* __restrict__ off, int32_t C, int32_t* __restrict__ cid) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = C;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    cid[i] = lo;
+  }
+}
+
+// build the batch description for clusters h_off[0..C] with softenings eps
+cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double* eps, Batch** out) {
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return cudaErrorMemoryAllocation;
+  b->C = C;
+  b->N = h_off[C];
+  b->h_off.assign(h_off, h_off + C + 1);
+  std::vector<int32_t> chc, clch0(C + 1);
+  std::vector<int64_t> chlo, chhi;
+  for (int32_t q = 0; q < C; ++q) {
+    clch0[q] = (int32_t)chc.size();
+    for (int64_t s = h_off[q]; s < h_off[q + 1]; s += kSelChunk) {
+      chc.push_back(q);
+      chlo.push_back(s);
+      chhi.push_back(std::min<int64_t>(s + kSelChunk, h_off[q + 1]));
+    }
+  }
+  clch0[C] = (int32_t)chc.size();
+  b->nchunks = (int32_t)chc.size();
+  std::vector<float> e2f(C);
+  std::vector<double> e2d(C);
+  for (int32_t q = 0; q < C; ++q) {
+    e2d[q] = eps[q] * eps[q];
+    e2f[q] = (float)e2d[q];
+  }
+  cudaError_t e = cudaSuccess;
+#define BA(p, n) \
+  if (e == cudaSuccess) e = dalloc(&(p), (n));
+  BA(b->off, C + 1) BA(b->eps2f, C) BA(b->eps2d, C) BA(b->cid, c->n_pad) BA(b->ch_cluster, b->nchunks)
+  BA(b->ch_lo, b->nchunks) BA(b->ch_hi, b->nchunks) BA(b->cl_ch0, C + 1) BA(b->ch_min, b->nchunks)
+  BA(b->ch_cnt, b->nchunks) BA(b->tnext, C) BA(b->nact, C) BA(b->itiles, C) BA(b->nsplit, C) BA(b->jps, C)
+  BA(b->item_off, C + 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
+#undef BA
+  auto H2D = [&](void* d, const void* h, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream);
+  };
+  H2D(b->off, h_off, (C + 1) * sizeof(int64_t));
+  H2D(b->eps2f, e2f.data(), C * sizeof(float));
+  H2D(b->eps2d, e2d.data(), C * sizeof(double));
+  H2D(b->ch_cluster, chc.data(), chc.size() * sizeof(int32_t));
+  H2D(b->ch_lo, chlo.data(), chlo.size() * sizeof(int64_t));
+  H2D(b->ch_hi, chhi.data(), chhi.size() * sizeof(int64_t));
+  H2D(b->cl_ch0, clch0.data(), clch0.size() * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream);
+  if (e == cudaSuccess && b->N > 0) {
+    fill_cid<<<grid_for(b->N, 256, 4096), 256, 0, c->stream>>>(b->N, b->off, C, b->cid);
+    e = cudaGetLastError();
+  }
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<kMixNT, kMixIPT, kMixJT>, kMixNT, 0);
+  b->grid_mixed = std::max(1, per_sm) * c->sm_count;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<kF64NT, kF64JT>, kF64NT, 0);
+  b->grid_fp64 = std::max(1, per_sm) * c->sm_count;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host vectors go out of scope
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+cudaError_t set_params(nb_ctx* c, Batch* b, double t_end) {
+  BParams p{t_end, c->eta, c->dt_min, c->dt_max, kMaxIters};
+  // pinned staging keeps the copy asynchronous-safe
+  memcpy(c->hpin, &p, sizeof(p));
+  cudaError_t e = cudaMemcpyAsync(b->prm, c->hpin, sizeof(p), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+// plan for the current active lists (b->nact, act), without loop control
+cudaError_t plan_only(nb_ctx* c, Batch* b) {
+  const bool mixed = c->precision == NB_MIXED;
+  const int per_cta = mixed ? kMixNT * kMixIPT : kF64NT;
+  const int jt = mixed ? kMixJT : kF64JT;
+  const int grid = mixed ? b->grid_mixed : b->grid_fp64;
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
+                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride, b->ctrl,
+                                    b->prm, c->status, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
+  const bool mixed = c->precision == NB_MIXED;
+  const int g = grid_for(b->N, 256, c->sm_count * 16);
+  b_predict<<<g, 256, 0, c->stream>>>(b->N, c->n_pad, b->cid, b->nact, b->tnext, own_time ? 1 : 0, c->m, c->x,
+                                      c->v, c->a, c->jk, c->t, c->xp, c->vp, c->jA, c->jB, c->jC, 1, mixed ? 1 : 0);
+  if (mixed)
+    b_force_mixed<kMixNT, kMixIPT, kMixJT><<<b->grid_mixed, kMixNT, 0, c->stream>>>(
+        b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+  else
+    b_force_fp64<kF64NT, kF64JT><<<b->grid_fp64, kF64NT, 0, c->stream>>>(
+        b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+  b_reduce<<<g, 256, 0, c->stream>>>(b->N, b->cid, b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part,
+                                     c->F, c->n_pad);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+// one block step of every active cluster, all on the device
+cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle, int use_handle) {
+  const bool mixed = c->precision == NB_MIXED;
+  const int per_cta = mixed ? kMixNT * kMixIPT : kF64NT;
+  const int jt = mixed ? kMixJT : kF64JT;
+  const int grid = mixed ? b->grid_mixed : b->grid_fp64;
+  b_sel_min<<<b->nchunks, 256, 0, c->stream>>>(b->ch_lo, b->ch_hi, c->t, c->dt, b->ch_min);
+  b_sel_count<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min, c->t,
+                                                 c->dt, b->tnext, b->ch_cnt);
+  b_sel_write<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_cnt, b->off,
+                                                 c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
+                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride, b->ctrl,
+                                    b->prm, c->status, handle, use_handle);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = body_after_plan(c, b, false)) != cudaSuccess) return e;
+  const int g = grid_for(b->N, 128, c->sm_count * 32);
+  b_correct<<<g, 128, 0, c->stream>>>(b->N, c->n_pad, b->cid, b->off, b->nact, b->tnext, c->act, c->F, c->n_pad,
+                                      b->prm, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->status);
+  c->launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t build_graph(nb_ctx* c, Batch* b) {
+  if (b->exec && b->exec_precision == c->precision) return cudaSuccess;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  // zero-initialised parameter block (the struct has no usable default constructor)
+  alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+  memset(np_buf, 0, sizeof(np_buf));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const int64_t launches = c->launches;
+      cudaError_t ec = capture_step(c, b, h, 1);
+      c->launches = launches;
+      cudaGraph_t got = nullptr;
+      e = cudaStreamEndCapture(c->stream, &got);
+      if (ec != cudaSuccess) e = ec;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) b->exec_precision = c->precision;
+  return e;
+}
+
+int finish_status(nb_ctx* c) {
+  nb_dev_status st;
+  if (cudaMemcpyAsync(c->hpin, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return NB_ECUDA;
+  memcpy(&st, c->hpin, sizeof(st));
+  if (st.flags & NB_ST_TIMEOUT) return NB_ETIMEOUT;
+  if (st.flags & NB_ST_NUMERIC) return NB_ENUMERIC;
+  return NB_OK;
+}
+
+int64_t read_ctrl(nb_ctx* c, Batch* b, int idx) {
+  int64_t v = 0;
+  if (cudaMemcpyAsync(c->hpin, b->ctrl + idx, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream) == cudaSuccess &&
+      cudaStreamSynchronize(c->stream) == cudaSuccess)
+    memcpy(&v, c->hpin, sizeof(v));
+  return v;
+}
+
+// graph-driven integration of every cluster of b to t_end
+int run_graph(nb_ctx* c, Batch* b, double t_end) {
+  if (set_params(c, b, t_end) != cudaSuccess) return NB_ECUDA;
+  if (build_graph(c, b) != cudaSuccess) {
+    cudaGetLastError();
+    return NB_ECUDA;
+  }
+  if (cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream) != cudaSuccess) return NB_ECUDA;
+  if (cudaGraphLaunch(b->exec, c->stream) != cudaSuccess) return NB_ECUDA;
+  const int64_t iters = read_ctrl(c, b, 1);
+  const int64_t inter = read_ctrl(c, b, 2);
+  c->steps += iters > 0 ? iters - 1 : 0;
+  c->interactions += (double)inter;
+  c->launches += iters * 8;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return finish_status(c);
+}
+
+// all particles of every cluster at their own time (Sec. 4.1 step 1): F = forces
+cudaError_t all_forces(nb_ctx* c, Batch* b) {
+  cudaError_t e0 = cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream);
+  if (e0 != cudaSuccess) return e0;
+  b_all_active<<<grid_for(b->N, 256, 4096), 256, 0, c->stream>>>(b->C, b->off, b->N, c->act, b->nact, b->tnext);
+  cudaError_t e = plan_only(c, b);
+  if (e != cudaSuccess) return e;
+  c->launches += 2;
+  return body_after_plan(c, b, true);
+}
+
+// copy rows [src + o, src + o + n) of every SoA array between contexts
+cudaError_t copy_state(nb_ctx* dst, int64_t dofs, const nb_ctx* src, int64_t sofs, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  struct R {
+    double* d;
+    const double* s;
+    int rows;
+  } rs[] = {{dst->m, src->m, 1},   {dst->x, src->x, 3},     {dst->v, src->v, 3}, {dst->a, src->a, 3},
+            {dst->jk, src->jk, 3}, {dst->pot, src->pot, 1}, {dst->t, src->t, 1}, {dst->dt, src->dt, 1}};
+  for (const R& r : rs)
+    for (int k = 0; k < r.rows; ++k) {
+      cudaError_t e = cudaMemcpyAsync(r.d + k * dst->n_pad + dofs, r.s + k * src->n_pad + sofs, n * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+void nb_ensemble_free(nb_ctx* c) {
+  if (!c) return;
+  batch_free(batch_of(c));
+  c->ens = nullptr;
+}
+
+int nb_integrate_graph(nb_ctx* c, double t_end) {
+  Batch* b = batch_of(c);
+  if (c->n_clusters == 0 && (!b || b->N != c->n)) {
+    batch_free(b);
+    c->ens = nullptr;
+    const int64_t off[2] = {0, c->n};
+    const double eps = c->eps;
+    if (batch_build(c, 1, off, &eps, &b) != cudaSuccess) return NB_ECUDA;
+    c->ens = b;
+  }
+  if (c->n_clusters == 0) {  // the softening may have changed since the batch was built
+    const double e2 = c->eps * c->eps;
+    const float e2f = (float)e2;
+    if (cudaMemcpyAsync(b->eps2d, &e2, sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->eps2f, &e2f, sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return NB_ECUDA;
+  }
+  return run_graph(c, b, t_end);
+}
+
+extern "C" {
+
+int nb_ensemble_create(nb_ctx** out, int32_t n_clusters, const int64_t* offsets, const double* eps, int precision,
+                       int device, void* cuda_stream) {
+  if (!out) return NB_EINVAL;
+  *out = nullptr;
+  if (n_clusters < 1 || !offsets || !eps || offsets[0] != 0) return NB_EINVAL;
+  for (int32_t q = 0; q < n_clusters; ++q)
+    if (offsets[q + 1] <= offsets[q] || !(eps[q] > 0.0) || !isfinite(eps[q])) return NB_EINVAL;
+  nb_ctx* c = nullptr;
+  int r = nb_create(&c, offsets[n_clusters], precision, device, cuda_stream);
+  if (r != NB_OK) return r;
+  Batch* b = nullptr;
+  if (batch_build(c, n_clusters, offsets, eps, &b) != cudaSuccess) {
+    nb_destroy(c);
+    return NB_ENOMEM;
+  }
+  c->ens = b;
+  c->n_clusters = n_clusters;
+  c->h_offsets = (int64_t*)malloc((n_clusters + 1) * sizeof(int64_t));
+  c->h_ceps = (double*)malloc(n_clusters * sizeof(double));
+  if (!c->h_offsets || !c->h_ceps) {
+    nb_destroy(c);
+    return NB_ENOMEM;
+  }
+  memcpy(c->h_offsets, offsets, (n_clusters + 1) * sizeof(int64_t));
+  memcpy(c->h_ceps, eps, n_clusters * sizeof(double));
+  *out = c;
+  return NB_OK;
+}
+
+int nb_ensemble_initial_forces_and_dt(nb_ctx* c) {
+  if (!c || !c->ens) return NB_EINVAL;
+  Batch* b = batch_of(c);
+  if (c->n < b->N) return NB_ESTATE;
+  if (set_params(c, b, 0.0) != cudaSuccess) return NB_ECUDA;
+  if (all_forces(c, b) != cudaSuccess) return NB_ECUDA;
+  b_initial_dt<<<grid_for(b->N, 256, c->sm_count * 16), 256, 0, c->stream>>>(b->N, c->n_pad, c->F, c->n_pad, b->prm,
+                                                                             c->a, c->jk, c->pot, c->t, c->dt,
+                                                                             c->status);
+  c->launches += 1;
+  if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
+  c->interactions += (double)read_ctrl(c, b, 2);
+  return finish_status(c);
+}
+
+int nb_ensemble_energy(nb_ctx* c, double* ekin, double* epot) {
+  if (!c || !c->ens || !ekin || !epot) return NB_EINVAL;
+  Batch* b = batch_of(c);
+  if (c->n < b->N) return NB_ESTATE;
+  if (set_params(c, b, 0.0) != cudaSuccess) return NB_ECUDA;
+  if (all_forces(c, b) != cudaSuccess) return NB_ECUDA;
+  b_energy<<<b->C, 256, 0, c->stream>>>(b->off, c->n_pad, c->m, c->v, c->F, c->n_pad, b->esum);
+  c->launches += 1;
+  std::vector<double> h(2 * (size_t)b->C);
+  if (cudaMemcpyAsync(h.data(), b->esum, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return NB_ECUDA;
+  for (int32_t q = 0; q < b->C; ++q) {
+    ekin[q] = h[2 * q];
+    epot[q] = h[2 * q + 1];
+  }
+  c->pred_valid = false;
+  c->f_valid = false;
+  return finish_status(c);
+}
+
+int nb_ensemble_integrate(nb_ctx* c, double t_end, int mode) {
+  if (!c || !c->ens || c->n_clusters == 0) return NB_EINVAL;
+  Batch* b = batch_of(c);
+  if (!(t_end > 0.0) || !isfinite(t_end) || fmod(t_end, c->dt_max) != 0.0) return NB_EINVAL;
+  if (c->n < b->N) return NB_ESTATE;
+  if (mode == NB_ENSEMBLE_PERSISTENT) return run_graph(c, b, t_end);
+  if (mode != NB_ENSEMBLE_PER_CLUSTER) return NB_EINVAL;
+  // reference: each cluster integrated on its own with host-driven per-step launches
+  if (!b->child) {
+    int64_t nmax = 0;
+    for (int32_t q = 0; q < b->C; ++q) nmax = std::max(nmax, b->h_off[q + 1] - b->h_off[q]);
+    int r = nb_create(&b->child, nmax, c->precision, c->device, (void*)c->stream);
+    if (r != NB_OK) return r;
+  }
+  nb_ctx* ch = b->child;
+  nb_set_precision(ch, c->precision);
+  for (int32_t q = 0; q < b->C; ++q) {
+    const int64_t o = b->h_off[q], n = b->h_off[q + 1] - o;
+    if (copy_state(ch, 0, c, o, n, c->stream) != cudaSuccess) return NB_ECUDA;
+    ch->n = n;
+    ch->pred_valid = ch->f_valid = false;
+    int r = nb_set_params(ch, c->h_ceps[q], c->eta, c->dt_min, c->dt_max);
+    if (r == NB_OK) r = nb_integrate(ch, t_end, 0);
+    if (r != NB_OK) return r;
+    if (copy_state(c, o, ch, 0, n, c->stream) != cudaSuccess) return NB_ECUDA;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NB_ECUDA;
+  c->interactions += ch->interactions;
+  c->launches += ch->launches;
+  c->steps += ch->steps;
+  ch->interactions = 0;
+  ch->launches = 0;
+  ch->steps = 0;
+  return finish_status(c);
+}
+
+}  // extern "C"

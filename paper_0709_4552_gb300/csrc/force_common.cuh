@@ -1,0 +1,306 @@
+// force_common.cuh -- the direct-sum force "work item" (Sec. 4.1 step 4,
+// Eq. 3) shared by every launch shape: the grid kernels of the host-driven
+// path, the persistent kernels of the graph-driven loop and of the batched
+// ensemble.  One item = one i-tile (NT*IPT active particles of one list)
+// against one contiguous j-range [jlo, jhi) of the j-store.
+//
+// For each active i and every j != i (Plummer softening eps, G = 1):
+//   r = x_j - x_i, w = v_j - v_i, s^2 = r.r + eps^2,
+//   acc += m_j r / s^3,  jerk += m_j (w / s^3 - 3 (r.w) r / s^5),  pot -= m_j / s.
+// Items sum +m/s; the sign of the potential is applied when the item is
+// final (one split) or by the split reduction.
+//
+// Mixed path: positions are double-single pairs (hi, lo) written by the
+// predictor; r = (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo) is the FP64 difference
+// rounded to FP32 within about an ulp (hi difference exact for close pairs,
+// Sterbenz).  Pairwise arithmetic is FP32 with one hardware rsqrt (MUFU),
+// optionally refined by one Newton step (NB_MIXED_NEWTON).  The jerk term of
+// a pair is formed completely before it is accumulated: its two parts
+// (w / s^3 and -3 (r.w) r / s^5) cancel for close pairs, and adding them to
+// the running sum one after the other costs up to 4x in the worst particle's
+// error.  FP32 partial sums over one j-tile (JT pairs) are folded into FP64
+// accumulators.  j-tiles (40 B per particle: float4
+// hi+m, float4 lo+vx, float2 vy vz) are staged in shared memory with cp.async
+// double buffering and read as warp-wide broadcasts.
+//
+// FP64 path: every operation in IEEE FP64, 1/s from an FP32 seed refined in
+// FP64; per-tile FP64 partials folded into (hi, lo) accumulators with Knuth's
+// TwoSum.  On GB300 the FP64 pipe issues 2 FMA/clk/SM (1/64 of FP32), which
+// bounds this path.
+//
+// Self pair: excluded by index, as in the definition.  Mixed path: only the
+// j-tile holding one of a warp's own i needs the test, so a warp vote picks a
+// masked copy of the inner loop for that tile (no per-pair cost elsewhere).
+//
+// Ragged j-ranges: a tile reaching past jhi loads clamped (in-bounds)
+// addresses and the slots past jhi are overwritten with a massless particle
+// far away, which contributes exactly zero.
+#pragma once
+
+#include "nb_internal.cuh"
+
+// one Newton step on the hardware rsqrt in the mixed path (1 = on)
+#ifndef NB_MIXED_NEWTON
+#define NB_MIXED_NEWTON 0
+#endif
+
+namespace nbk {
+
+constexpr float kFarF = 1.0e15f;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int JT>
+struct MixedSmem {
+  float4 A[2][JT];
+  float4 B[2][JT];
+  float2 C[2][JT];
+};
+
+template <int NT, int JT>
+__device__ __forceinline__ void mixed_load_tile(float4* sA, float4* sB, float2* sC, const float4* __restrict__ jA,
+                                                const float4* __restrict__ jB, const float2* __restrict__ jC,
+                                                int64_t j0, int64_t jhi) {
+#pragma unroll
+  for (int q = threadIdx.x; q < JT; q += NT) {
+    const int64_t j = min(j0 + q, jhi - 1);
+    cp_async16(&sA[q], &jA[j]);
+    cp_async16(&sB[q], &jB[j]);
+    cp_async8(&sC[q], &jC[j]);
+  }
+}
+
+// One j-tile against the thread's IPT i-particles; FP32 partials in p.
+template <int IPT, int JT, bool MASK>
+__device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, const float4* __restrict__ sB,
+                                                const float2* __restrict__ sC, const float (&xh)[IPT][3],
+                                                const float (&xl)[IPT][3], const float (&vi)[IPT][3],
+                                                const int (&rel)[IPT], float eps2, float (&p)[IPT][7]) {
+#pragma unroll 4
+  for (int q = 0; q < JT; ++q) {
+    const float4 A = sA[q];
+    const float4 B = sB[q];
+    const float2 C = sC[q];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const float dx = (A.x - xh[k][0]) + (B.x - xl[k][0]);
+      const float dy = (A.y - xh[k][1]) + (B.y - xl[k][1]);
+      const float dz = (A.z - xh[k][2]) + (B.z - xl[k][2]);
+      const float wx = B.w - vi[k][0];
+      const float wy = C.x - vi[k][1];
+      const float wz = C.y - vi[k][2];
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+      const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+#if NB_MIXED_NEWTON
+      // hardware 1/sqrt + one Newton step: e = 1 - s^2 y0^2, y = y0 + y0 e / 2
+      const float y0 = nb_rsqrt_approx(r2);
+      const float e = fmaf(-r2, y0 * y0, 1.0f);
+      float rinv = fmaf(0.5f, y0 * e, y0);
+#else
+      float rinv = nb_rsqrt_approx(r2);
+#endif
+      if (MASK) rinv = (q == rel[k]) ? 0.0f : rinv;
+      const float rinv2 = rinv * rinv;
+      const float mr = A.w * rinv;
+      const float mr3 = mr * rinv2;
+      // jerk term formed before accumulation: u = w - 3 (r.w)/s^2 r; the two
+      // parts cancel for close pairs, so they must not enter the sum apart
+      const float a3 = (rw * -3.0f) * rinv2;
+      p[k][6] += mr;
+      p[k][0] = fmaf(mr3, dx, p[k][0]);
+      p[k][1] = fmaf(mr3, dy, p[k][1]);
+      p[k][2] = fmaf(mr3, dz, p[k][2]);
+      p[k][3] = fmaf(mr3, fmaf(a3, dx, wx), p[k][3]);
+      p[k][4] = fmaf(mr3, fmaf(a3, dy, wy), p[k][4]);
+      p[k][5] = fmaf(mr3, fmaf(a3, dz, wz), p[k][5]);
+    }
+  }
+}
+
+// Mixed-precision item: i-tile starting at list position ibase (n entries in
+// list, entries clamped to [0, idx_hi)), j-range [jlo, jhi).  Writes 7 rows
+// out[c * ostride + pos] (final: acc, jerk, pot with its sign) or raw sums.
+template <int NT, int IPT, int JT>
+__device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __restrict__ jA,
+                                           const float4* __restrict__ jB, const float2* __restrict__ jC,
+                                           int64_t jlo, int64_t jhi, int64_t idx_hi,
+                                           const int32_t* __restrict__ list, int64_t n, int64_t ibase,
+                                           float eps2, double* __restrict__ out, int64_t ostride,
+                                           bool finalize) {
+  const int tid = threadIdx.x;
+  float xh[IPT][3], xl[IPT][3], vi[IPT][3];
+  int64_t self[IPT];
+  double acc[IPT][7];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    int64_t pos = ibase + k * NT + tid;
+    if (pos >= n) pos = n - 1;
+    int64_t p = list[pos];
+    p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
+    self[k] = p;
+    const float4 A = jA[p], B = jB[p];
+    const float2 C = jC[p];
+    xh[k][0] = A.x; xh[k][1] = A.y; xh[k][2] = A.z;
+    xl[k][0] = B.x; xl[k][1] = B.y; xl[k][2] = B.z;
+    vi[k][0] = B.w; vi[k][1] = C.x; vi[k][2] = C.y;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc[k][c] = 0.0;
+  }
+
+  const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
+  if (ntiles > 0) mixed_load_tile<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
+  cp_async_commit();
+
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int buf = tile & 1;
+    const int64_t jt = jlo + (int64_t)tile * JT;
+    if (tile + 1 < ntiles)
+      mixed_load_tile<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    if (jt + JT > jhi) {  // ragged last tile: massless far-away particles past jhi
+      for (int q = tid; q < JT; q += NT)
+        if (jt + q >= jhi) sm.A[buf][q] = make_float4(kFarF, kFarF, kFarF, 0.0f);
+      __syncthreads();
+    }
+
+    int rel[IPT];
+    bool hit = false;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int64_t d = self[k] - jt;
+      rel[k] = (d >= 0 && d < JT) ? (int)d : -1;
+      hit = hit || rel[k] >= 0;
+    }
+    float p[IPT][7];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) p[k][c] = 0.0f;
+
+    if (__any_sync(0xffffffffu, hit))
+      mixed_tile_pass<IPT, JT, true>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+    else
+      mixed_tile_pass<IPT, JT, false>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) acc[k][c] += (double)p[k][c];
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int64_t pos = ibase + k * NT + tid;
+    if (pos >= n) continue;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) out[c * ostride + pos] = acc[k][c];
+    out[6 * ostride + pos] = finalize ? -acc[k][6] : acc[k][6];
+  }
+}
+
+template <int JT>
+struct Fp64Smem {
+  double x[3][JT], v[3][JT], m[JT];
+};
+
+// FP64 item: one i per thread (i-tile of NT), j-range [jlo, jhi) with a
+// ragged tail filled by massless far-away particles.  xp, vp are SoA rows of
+// stride n_pad.
+template <int NT, int JT>
+__device__ __forceinline__ void fp64_item(Fp64Smem<JT>& sm, const double* __restrict__ xp,
+                                          const double* __restrict__ vp, const double* __restrict__ m,
+                                          int64_t n_pad, int64_t jlo, int64_t jhi,
+                                          const int32_t* __restrict__ list, int64_t n, int64_t ibase,
+                                          double eps2, double* __restrict__ out, int64_t ostride,
+                                          bool finalize) {
+  const int tid = threadIdx.x;
+  const int64_t pos0 = ibase + tid;
+  const int64_t pos = pos0 < n ? pos0 : n - 1;
+  int64_t self = list[pos];
+  self = self < 0 ? 0 : (self >= n_pad ? n_pad - 1 : self);  // a bad list never reads out of bounds
+  double xi[3], vi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xi[c] = xp[c * n_pad + self];
+    vi[c] = vp[c * n_pad + self];
+  }
+  double hi[7], lo[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) hi[c] = lo[c] = 0.0;
+
+  for (int64_t jt = jlo; jt < jhi; jt += JT) {
+    __syncthreads();
+    for (int q = tid; q < JT; q += NT) {
+      const int64_t j = jt + q;
+      if (j < jhi) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sm.x[c][q] = xp[c * n_pad + j];
+          sm.v[c][q] = vp[c * n_pad + j];
+        }
+        sm.m[q] = m[j];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sm.x[c][q] = (double)kFarF;
+          sm.v[c][q] = 0.0;
+        }
+        sm.m[q] = 0.0;
+      }
+    }
+    __syncthreads();
+    double p[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) p[c] = 0.0;
+#pragma unroll 2
+    for (int q = 0; q < JT; ++q) {
+      const double dx = sm.x[0][q] - xi[0], dy = sm.x[1][q] - xi[1], dz = sm.x[2][q] - xi[2];
+      const double wx = sm.v[0][q] - vi[0], wy = sm.v[1][q] - vi[1], wz = sm.v[2][q] - vi[2];
+      const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+      const double rw = fma(dz, wz, fma(dy, wy, dx * wx));
+      // the self pair (j == i) gets 1/s = 0, also when eps = 0
+      const double rinv = (jt + q == self) ? 0.0 : nb_rsqrt_fp64(r2);
+      const double rinv2 = rinv * rinv;
+      const double mr = sm.m[q] * rinv;
+      const double mr3 = mr * rinv2;
+      const double a3 = (rw * -3.0) * rinv2;  // jerk term formed before accumulation
+      p[6] += mr;
+      p[0] = fma(mr3, dx, p[0]);
+      p[1] = fma(mr3, dy, p[1]);
+      p[2] = fma(mr3, dz, p[2]);
+      p[3] = fma(mr3, fma(a3, dx, wx), p[3]);
+      p[4] = fma(mr3, fma(a3, dy, wy), p[4]);
+      p[5] = fma(mr3, fma(a3, dz, wz), p[5]);
+    }
+    // TwoSum fold (Knuth): hi + p = s + e exactly
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      const double s = hi[c] + p[c];
+      const double bp = s - hi[c];
+      const double e = (hi[c] - (s - bp)) + (p[c] - bp);
+      hi[c] = s;
+      lo[c] += e;
+    }
+  }
+  __syncthreads();  // the caller may reuse shared memory for its next item
+  if (pos0 >= n) return;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[c * ostride + pos0] = hi[c] + lo[c];
+  out[6 * ostride + pos0] = finalize ? -(hi[6] + lo[6]) : hi[6] + lo[6];
+}
+
+}  // namespace nbk

@@ -1,0 +1,158 @@
+// nb_internal.cuh -- context layout and kernel launchers shared by the
+// translation units of libnbody (the GB300 direct-sum Hermite engine).
+//
+// HBM layout of one context (n_max particles, n_pad = n_max rounded up to
+// NB_JPAD so that every j-tile is full; padding particles have m = 0 and sit
+// far away, so they contribute exactly zero):
+//
+//   master state, FP64 structure-of-arrays (component-major):
+//     m[n_pad], x[3][n_pad], v[3][n_pad], a[3][n_pad], jk[3][n_pad],
+//     pot[n_pad], t[n_pad], dt[n_pad]                        128 B/particle
+//   predicted j-particles (predictor output, Sec. 4.1 step 3):
+//     FP64 path:  xp[3][n_pad], vp[3][n_pad]                  48 B/particle
+//     mixed path: jA[n_pad] = float4(x_hi, y_hi, z_hi, m)
+//                 jB[n_pad] = float4(x_lo, y_lo, z_lo, vx)
+//                 jC[n_pad] = float2(vy, vz)                    40 B/particle
+//   force results of the last call, by position k in the active list:
+//     F[7][n_pad] = (ax, ay, az, jx, jy, jz, pot), FP64        56 B/particle
+//   split-j partial sums: part[n_split][7][n_i]                (bounded)
+//   active list: act[n_pad] (int32, ascending), identity list ident[n_pad]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+#define NB_JPAD 1024          // j-store padding granule (max j-tile)
+#define NB_PAD_POS 1.0e15     // position of padding particles (m = 0)
+
+// device status word bits
+#define NB_ST_NUMERIC 1u
+#define NB_ST_TIMEOUT 2u
+#define NB_ST_BADLIST 4u
+
+struct nb_dev_status {
+  unsigned int flags;          // NB_ST_* bits, sticky until cleared
+  unsigned int pad;
+  unsigned long long dt_underflows;
+};
+
+struct nb_tuning {
+  int ipt;      // i-particles per thread
+  int threads;  // threads per CTA
+  int jtile;    // j-particles per shared-memory tile
+  int nsplit;   // split-j factor (0 = automatic)
+};
+
+struct nb_tune_entry {
+  int64_t n_lo, n_hi;  // active-block size range this entry covers
+  nb_tuning cfg;
+};
+
+struct nb_ctx {
+  int device;
+  int precision;
+  int sm_count;
+  cudaStream_t stream;
+  bool own_stream;
+  int64_t n_max, n_pad, n;
+  double eps, eta, dt_min, dt_max;
+  int last_error;
+
+  // master state
+  double *m, *x, *v, *a, *jk, *pot, *t, *dt;
+  // predicted
+  double *xp, *vp;
+  float4 *jA, *jB;
+  float2 *jC;
+  double t_pred;         // time of the last prediction
+  bool pred_valid;
+  // forces of the last call
+  double* F;             // [7][n_pad]
+  int64_t f_n;           // size of the list of the last force call
+  bool f_valid;
+  const int32_t* f_list; // device list the forces belong to (act / ident / user copy)
+  // split-j scratch
+  double* part;
+  int64_t part_elems;    // capacity in doubles
+  // lists
+  int32_t *act, *ident, *ulist;   // ulist: device copy of a caller's host list
+  // block selection scratch
+  unsigned long long* sel_min;  // per-CTA minima [sel_ctas] + result at [sel_ctas]
+  int32_t* sel_cnt;             // per-CTA counts [sel_ctas] + total at [sel_ctas]
+  int sel_ctas;
+  double* red;                  // reduction scratch [2 * 1024]
+  // device status
+  nb_dev_status* status;
+  // pinned host staging for small results
+  void* hpin;
+  // timings
+  cudaEvent_t ev[8];
+  double ms_pred, ms_force, ms_corr, interactions;
+  bool ev_pending;           // step events recorded but not yet read
+  int64_t launches;          // kernels launched by this context (all launchers)
+  int64_t steps;             // block steps taken
+  // tuning
+  nb_tuning tune_override;   // all-zero = automatic
+  nb_tune_entry tune_table[16];
+  int tune_count;
+
+  // ensemble
+  int32_t n_clusters;
+  int64_t* d_offsets;   // [n_clusters + 1]
+  double* d_ceps;       // [n_clusters]
+  int64_t* h_offsets;
+  double* h_ceps;
+  void* ens;            // ensemble work area (ensemble.cu)
+};
+
+// ---- launchers (integrator.cu) -------------------------------------------
+cudaError_t nb_launch_predict(nb_ctx* c, double t, bool own_time);
+cudaError_t nb_launch_select(nb_ctx* c);    // writes act, sel_cnt[total], sel_min[result]
+cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t);
+cudaError_t nb_launch_initial_dt(nb_ctx* c);
+cudaError_t nb_launch_store_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
+cudaError_t nb_launch_energy(nb_ctx* c, const double* d_pot, double* d_out2);
+cudaError_t nb_launch_fill_ident(nb_ctx* c);
+cudaError_t nb_launch_aos_to_soa(const double* src, double* dst, int64_t count, int64_t stride_dst,
+                                 cudaStream_t s);
+cudaError_t nb_launch_soa_to_aos(const double* src, int64_t stride_src, double* dst, int64_t count,
+                                 cudaStream_t s);
+cudaError_t nb_launch_check_list(const int32_t* d_list, int64_t n, int64_t N, unsigned int* d_flag,
+                                 cudaStream_t s);
+
+// ---- launchers (force_fp64.cu / force_mixed.cu) ----------------------------
+// forces on the list d_list[0..n) from all N j; results to c->F
+cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
+cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
+// split-j reduction (force_fp64.cu): part[S][7][n] -> F in fixed order, potential sign
+cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit,
+                                   int64_t stride);
+bool nb_tuning_supported(int precision, const nb_tuning& cfg);
+nb_tuning nb_default_tuning(int precision);
+int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg);
+
+// the force dispatcher (capi.cu): picks the tuning and precision path
+cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
+
+// ensemble.cu
+void nb_ensemble_free(nb_ctx* c);
+int nb_integrate_graph(nb_ctx* c, double t_end);
+
+// ---- device helpers ---------------------------------------------------------
+__device__ __forceinline__ float nb_rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 1/sqrt(x) in FP64 for x in the float normal range: FP32 hardware seed
+// refined by one 2nd-order Newton-Raphson (Householder) step,
+//   e = 1 - x y0^2,  y = y0 (1 + e/2 + 3 e^2 / 8),
+// whose relative error is O(e^3) ~ 2^-63 for |e| <= 2^-21.
+__device__ __forceinline__ double nb_rsqrt_fp64(double x) {
+  const double y0 = (double)nb_rsqrt_approx((float)x);
+  const double e = fma(-x, y0 * y0, 1.0);
+  return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}

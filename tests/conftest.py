@@ -18,3 +18,17 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)
+
+
+@pytest.fixture(scope="session")
+def nbl():
+    """The CUDA library binding (built in-tree); GPU tests only."""
+    from paper_0709_4552_gb300 import build
+    build.build()
+    from paper_0709_4552_gb300 import nbody
+    nbody.lib()
+    return nbody

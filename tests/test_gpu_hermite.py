@@ -1,0 +1,239 @@
+"""Parity of the CUDA integrator (Sec. 4.1 steps 1-6: block selection,
+predictor, forces, Hermite corrector, power-of-two block steps of Sec. 2)
+with the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0709_4552_gb300 import inputs
+from _util import rel_scalar, rel_vec
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(nb, m, x, v, eps, eta, dt_min, dt_max, prec=None, state=None):
+    s = nb.NBody(len(m), nb.NB_FP64 if prec is None else prec, 0)
+    s.set_params(eps, eta, dt_min, dt_max)
+    if state is None:
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()
+    else:
+        s.set_j_particles(0, m, state["x"], state["v"], state["a"], state["jerk"], state["t"], state["dt"])
+    return s
+
+
+def _state(s, N):
+    return s.get_particles(0, N)
+
+
+def test_initial_steps_match(nbl):
+    N, eps = 700, 1 / 256
+    m, x, v = inputs.plummer(N, 201, "salpeter")
+    r = oracle.hermite_run(m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -3, 2.0 ** -3, max_block_steps=0,
+                           compensated=True)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -3) as s:
+        st = _state(s, N)
+    assert rel_vec(st["a"], r["a"]).max() < 1e-12
+    assert rel_vec(st["jerk"], r["jerk"]).max() < 1e-12
+    assert np.array_equal(st["dt"], r["dt"])
+    assert np.all(st["t"] == 0.0)
+
+
+@pytest.mark.parametrize("steps", [1, 40])
+def test_block_steps_match(nbl, steps):
+    # same block schedule (t, dt exactly) and state (FP64) after k block steps
+    N, eps = 1000, 1 / 256
+    m, x, v = inputs.plummer(N, 202, "salpeter")
+    r = oracle.hermite_run(m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -3, 1.0, max_block_steps=steps,
+                           compensated=True)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -3) as s:
+        for _ in range(steps):
+            s.step()
+        st = _state(s, N)
+    assert np.array_equal(st["t"], r["t"])
+    assert np.array_equal(st["dt"], r["dt"])
+    assert np.abs(st["x"] - r["x"]).max() < 1e-12
+    assert np.abs(st["v"] - r["v"]).max() < 1e-11
+
+
+def test_next_block_matches_definition(nbl):
+    N = 3000
+    m, x, v = inputs.plummer(N, 203, "salpeter")
+    with _ctx(nbl, m, x, v, 1 / 512, 0.01, 2.0 ** -22, 2.0 ** -3) as s:
+        for _ in range(5):
+            st = _state(s, N)
+            t, n, idx = s.next_block()
+            due = st["t"] + st["dt"]
+            assert t == due.min()
+            assert np.array_equal(idx, np.nonzero(due == t)[0].astype(np.int32))
+            assert n == len(idx)
+            s.step()
+
+
+def _energy(m, st, eps):
+    k, w = oracle.energy(m, st["x"], st["v"], eps)
+    return k + w
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config1_shared_steps(nbl, prec):
+    # Plummer N=1024, eps=1/256, shared dt=2^-10, 128 steps (full i=j each step)
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    N, eps, dt = 1024, 1 / 256, 2.0 ** -10
+    m, x, v = inputs.plummer(N, 1)
+    E0 = _energy(m, dict(x=x, v=v), eps)
+    r = oracle.hermite_run(m, x, v, eps, 0.01, dt, dt, 128 * dt, compensated=True)
+    assert r["block_steps"] == 128
+    dE_orc = abs(_energy(m, r, eps) - E0) / abs(E0)
+    with _ctx(nbl, m, x, v, eps, 0.01, dt, dt, prec=P) as s:
+        for k in range(128):
+            t, n = s.step()
+            assert n == N and t == (k + 1) * dt
+            if (k + 1) % 16 == 0:
+                # forces on the GPU's own state vs the oracle on that state
+                st = _state(s, N)
+                s.predict(t)
+                a, j, p = s.compute_forces(np.arange(N, dtype=np.int32))
+                ar, jr, pr = oracle.forces(m, st["x"], st["v"], eps, compensated=True)
+                tol = 1e-12 if P == nbl.NB_FP64 else 1e-5
+                assert rel_vec(a, ar).max() < tol and rel_vec(j, jr).max() < tol * 10
+                assert rel_scalar(p, pr).max() < tol
+        st = _state(s, N)
+    dE_gpu = abs(_energy(m, st, eps) - E0) / abs(E0)
+    print(f"config1 {prec}: |dE/E| gpu {dE_gpu:.3e} oracle {dE_orc:.3e}")
+    assert dE_gpu <= 2 * dE_orc + 1e-13
+    P_mom = (m[:, None] * st["v"]).sum(0)
+    assert np.abs(P_mom).max() < (1e-14 if P == nbl.NB_FP64 else 1e-9)
+    if P == nbl.NB_FP64:
+        assert np.abs(st["x"] - r["x"]).max() < 1e-10
+
+
+def _kepler():
+    e, rp = 0.5, 0.5
+    vp = math.sqrt(3.0)
+    m = np.array([0.5, 0.5])
+    x = np.array([[-rp / 2, 0, 0], [rp / 2, 0, 0]])
+    v = np.array([[0, -vp / 2, 0], [0, vp / 2, 0]])
+    return m, x, v
+
+
+def _kepler_sep(t, e=0.5):
+    Mq = math.fmod(t, 2 * math.pi)
+    E = Mq
+    for _ in range(60):
+        E -= (E - e * math.sin(E) - Mq) / (1 - e * math.cos(E))
+    return np.array([math.cos(E) - e, math.sqrt(1 - e * e) * math.sin(E), 0.0])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("mixed", 1e-4)])
+def test_kepler_orbit(nbl, prec, tol):
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    m, x, v = _kepler()
+    with _ctx(nbl, m, x, v, 0.0, 0.01, 2.0 ** -9, 2.0 ** -9, prec=P) as s:
+        s.integrate(64.0)
+        st = _state(s, 2)
+    sep = st["x"][1] - st["x"][0]
+    assert np.linalg.norm(sep - _kepler_sep(64.0)) < tol
+
+
+def test_integrate_equals_steps(nbl):
+    N, eps = 800, 1 / 256
+    m, x, v = inputs.plummer(N, 204)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -5) as s:
+        s.integrate(2.0 ** -5)
+        a = _state(s, N)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -5) as s:
+        while True:
+            st = _state(s, N)
+            if np.all(st["t"] == 2.0 ** -5):
+                break
+            s.step()
+        b = _state(s, N)
+    for k in ("x", "v", "a", "jerk", "t", "dt"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_checkpoint_resume_bitwise(nbl):
+    N, eps = 900, 1 / 256
+    m, x, v = inputs.plummer(N, 205, "salpeter")
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -4) as s:
+        for _ in range(30):
+            s.step()
+        mid = _state(s, N)
+        for _ in range(30):
+            s.step()
+        ref = _state(s, N)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -4, state=mid) as s:
+        for _ in range(30):
+            s.step()
+        got = _state(s, N)
+    for k in ("x", "v", "a", "jerk", "t", "dt"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_energy_matches_oracle(nbl):
+    N, eps = 2000, 1 / 256
+    m, x, v = inputs.plummer(N, 206, "salpeter")
+    k0, w0 = oracle.energy(m, x, v, eps)
+    with nbl.NBody(N, nbl.NB_FP64, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        k, w = s.energy()
+    assert abs(k - k0) / abs(k0) < 1e-13
+    assert abs(w - w0) / abs(w0) < 1e-12
+
+
+@pytest.mark.slow
+def test_config2_reduced_energy_drift(nbl):
+    # config-2 physics at N=16384 (Salpeter, eps=1/1024, eta=0.01, 2^-22..2^-3) to t=1/64
+    N, eps, t_end = 16384, 1 / 1024, 2.0 ** -6
+    m, x, v = inputs.plummer(N, 2, "salpeter")
+    E0 = _energy(m, dict(x=x, v=v), eps)
+    r = oracle.hermite_run(m, x, v, eps, 0.01, 2.0 ** -22, t_end, t_end)
+    dE_orc = abs(_energy(m, r, eps) - E0) / abs(E0)
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, t_end) as s:
+        s.integrate(t_end)
+        st = _state(s, N)
+        idx = inputs.sample_indices(N, 4096, 1002)
+        s.predict(t_end)
+        a, j, p = s.compute_forces(idx.astype(np.int32))
+    ar, jr, pr = oracle.forces(m, st["x"], st["v"], eps, idx=idx, compensated=True)
+    assert rel_vec(a, ar).max() < 1e-12 and rel_vec(j, jr).max() < 1e-12
+    dE_gpu = abs(_energy(m, st, eps) - E0) / abs(E0)
+    print(f"config2@16k: |dE/E| gpu {dE_gpu:.3e} oracle {dE_orc:.3e}")
+    assert dE_gpu <= 2 * dE_orc + 1e-13
+
+
+def test_nan_input_reported(nbl):
+    torch = pytest.importorskip("torch")
+    N = 256
+    m, x, v = inputs.plummer(N, 207)
+    v = v.copy()
+    v[17, 0] = np.nan
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        s.set_j_particles(0, dev(m), dev(x), dev(v))   # device input: not validated
+        torch.cuda.synchronize()
+        with pytest.raises(nbl.NBodyError) as e:
+            s.initial_forces_and_dt()
+        assert e.value.code == nbl.NB_ENUMERIC
+        code, _ = s.check_device_status()
+        assert code == nbl.NB_ENUMERIC
+        s.clear_error()
+        assert s.check_device_status()[0] == nbl.NB_OK
+
+
+def test_dt_underflow_counted(nbl):
+    # a tight unsoftened binary: its criterion falls below dt_min = 2^-12
+    m = np.array([0.5, 0.5, 1e-3])
+    x = np.array([[-1e-4, 0, 0], [1e-4, 0, 0], [1.0, 0, 0]])
+    vb = math.sqrt(0.5 / 2e-4) / 2 * 2
+    v = np.array([[0, -vb / 2, 0], [0, vb / 2, 0], [0, 0.5, 0]])
+    with _ctx(nbl, m, x, v, 0.0, 0.01, 2.0 ** -12, 2.0 ** -6) as s:
+        s.step()
+        code, under = s.check_device_status()
+        st = _state(s, 3)
+    assert code == nbl.NB_OK and under >= 2
+    assert st["dt"][0] == 2.0 ** -12 and st["dt"][1] == 2.0 ** -12
