@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="sampled i for the oracle legs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
     return ap.parse_args()
 
 
@@ -190,6 +191,8 @@ def main():
 
     s = nb.NBody(N, prec, local, stream=stream)
     s.set_params(eps, 0.01, dt_shared, dt_shared)
+    if args.tuning:
+        s.set_tuning(*[int(t) for t in args.tuning.split(",")])
     s.set_j_particles(0, m, x, v)
     s.initial_forces_and_dt()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -665,7 +665,11 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
 }
 
 cudaError_t set_params(nb_ctx* c, Batch* b, double t_end) {
-  BParams p{t_end, c->eta, c->dt_min, c->dt_max, kMaxIters};
+  // every block step moves the earliest particle forward by at least dt_min,
+  // so no run can need more than t_end / dt_min + 2 loop iterations
+  int64_t cap = (int64_t)ceil(t_end / c->dt_min) + 2;
+  if (cap > kMaxIters) cap = kMaxIters;
+  BParams p{t_end, c->eta, c->dt_min, c->dt_max, cap};
   // pinned staging keeps the copy asynchronous-safe
   memcpy(c->hpin, &p, sizeof(p));
   cudaError_t e = cudaMemcpyAsync(b->prm, c->hpin, sizeof(p), cudaMemcpyHostToDevice, c->stream);
