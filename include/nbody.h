@@ -273,6 +273,43 @@ int nb_ensemble_integrate(nb_ctx* ctx, double t_end, int mode);
  */
 int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
 
+/* ---- forces without any device allocation ------------------------------- */
+#define NB_NOALLOC_SCRATCH_DOUBLES (1 << 22)   /* fixed scratch: 32 MiB per GPU  */
+#define NB_NOALLOC_MAX_ACTIVE      (1 << 19)   /* largest active block accepted  */
+
+/*
+ * nb_forces_fp64_noalloc -- the paper has no counterpart to this call; it is
+ * a service for callers that cannot allocate device memory: applications
+ * that own all device memory themselves (their own pool, no cudaMalloc from
+ * libraries) and latency-critical loops where an allocation could stall or
+ * fail mid-run.  Such callers cannot use nb_create, which allocates.
+ *
+ * Computes the same FP64 acceleration, jerk and potential as
+ * nb_compute_forces with NB_FP64 (softening eps >= 0, j == i excluded) for
+ * the n active particles i_idx[0..n) from all N particles, with every buffer
+ * owned by the caller and resident on the current CUDA device: m[N],
+ * x[N][3], v[N][3] (positions/velocities at the common time), i_idx[n]
+ * (int32, each in [0, N)), outputs acc[n][3], jerk[n][3], pot[n] (any may be
+ * NULL).  Work is enqueued on cuda_stream (a cudaStream_t, NULL = default
+ * stream); the call returns without synchronising.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Split-j partial sums use one fixed array inside the library
+ * (NB_NOALLOC_SCRATCH_DOUBLES doubles, kept on every GPU that loads the
+ * library until the process exits).  The first call on a device does a
+ * one-time set-up: it looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current.  Make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * previous call's contents (every partial is written before it is read, so
+ * nothing needs clearing): calls whose work may overlap on the GPU race and
+ * must be ordered by the caller (one stream, or events).
+ * Errors: NB_EINVAL (N < 1, n < 0, n > N, n > NB_NOALLOC_MAX_ACTIVE -- the
+ * partial sums would not fit --, NULL inputs, eps < 0), NB_ECUDA.
+ */
+int nb_forces_fp64_noalloc(int64_t N, const double* m, const double* x, const double* v, double eps,
+                           const int32_t* i_idx, int64_t n, double* acc, double* jerk, double* pot,
+                           void* cuda_stream);
+
 /* nb_strerror -- static text for a status code (never NULL). */
 const char* nb_strerror(int code);
 

@@ -30,7 +30,7 @@ EXPORTS = (
     "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_last_error", "nb_clear_error",
     "nb_set_tuning", "nb_autotune", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
-    "nb_ensemble_integrate", "nb_ensemble_energy", "nb_strerror", "nb_version",
+    "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
 
 
@@ -89,6 +89,7 @@ def lib():
         "nb_ensemble_initial_forces_and_dt": (_int, [_vp]),
         "nb_ensemble_integrate": (_int, [_vp, _d, _int]),
         "nb_ensemble_energy": (_int, [_vp, _vp, _vp]),
+        "nb_forces_fp64_noalloc": (_int, [_i64, _vp, _vp, _vp, _d, _vp, _i64, _vp, _vp, _vp, _vp]),
         "nb_strerror": (ctypes.c_char_p, [_int]),
         "nb_version": (ctypes.c_char_p, []),
     }
@@ -327,6 +328,22 @@ def nb_ensemble_energy(ctx, n_clusters):
     w = np.empty(int(n_clusters))
     _check(lib().nb_ensemble_energy(ctx, k.ctypes.data_as(_vp), w.ctypes.data_as(_vp)), "nb_ensemble_energy")
     return k, w
+
+
+def nb_forces_fp64_noalloc(m, x, v, eps, i_idx, acc=None, jerk=None, pot=None, stream=None):
+    """FP64 forces from caller-owned CUDA tensors without any device
+    allocation by the library (for callers that manage all device memory
+    themselves).  m[N], x[N,3], v[N,3], i_idx[n] (int32) and the outputs
+    acc[n,3], jerk[n,3], pot[n] must be contiguous CUDA tensors; the work is
+    enqueued on ``stream`` (default: the legacy default stream)."""
+    n = int(i_idx.shape[0])
+    kind, p, keep = _marshal([m, x, v, i_idx, acc, jerk, pot],
+                             [np.float64, np.float64, np.float64, np.int32, np.float64, np.float64, np.float64])
+    if kind != NB_PTR_DEVICE:
+        raise TypeError("nb_forces_fp64_noalloc takes device (CUDA) tensors only")
+    s = None if stream is None else _vp(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().nb_forces_fp64_noalloc(int(m.shape[0]), p[0], p[1], p[2], float(eps), p[3], n, p[4], p[5],
+                                        p[6], s), "nb_forces_fp64_noalloc")
 
 
 class Ensemble:
