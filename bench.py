@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5"],
+                    help="c3 (default): the timed benchmark; c2/c4/c5: long integrations, one JSON line")
     return ap.parse_args()
 
 
@@ -165,11 +167,142 @@ def workload_config(args):
             "l2": "state read per step 0.35 GB > L2 (126 MB); L2 flushed (512 MB write) between steps"}
 
 
+def run_integration(args):
+    """Long block-step integrations of the other configurations (one GPU, one
+    JSON line each; not the headline metric):
+      c2: N=196608 Salpeter, eps=1/1024, eta=0.01, dt 2^-22..2^-3, FP64, to t=1/8;
+      c4: 512 clusters (N_c log-uniform 256..16384, seed 7, Salpeter,
+          eps_c=1/(4 N_c^(1/3))), mixed, to t=1/16: one CUDA-graph launch vs
+          per-cluster launches;
+      c5: N=2^22 Salpeter, eps=1/8192, mixed, to t=1/64 (wall x 64 = N-body time unit)."""
+    import torch
+    import oracle
+    from paper_0709_4552_gb300 import build, inputs
+    build.build()
+    oracle.build()
+    from paper_0709_4552_gb300 import nbody as nb
+    torch.cuda.set_device(0)
+    w = args.workload
+
+    def rel(a, b):
+        return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+    if w in ("c2", "c5"):
+        if w == "c2":
+            N, eps, t_end, seed, prec = 196608, 1.0 / 1024, 0.125, 2, nb.NB_FP64
+        else:
+            N, eps, t_end, seed, prec = 1 << 22, 1.0 / 8192, 1.0 / 64, 5, nb.NB_MIXED
+        m, x, v = inputs.plummer(N, seed, "salpeter")
+        s = nb.NBody(N, prec, 0)
+        s.set_params(eps, 0.01, 2.0 ** -22, min(0.125, t_end))
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()
+        k0, w0 = s.energy()
+        s.get_timings(reset=True)
+        c0 = s.get_counters()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.integrate(t_end, use_graph=True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        tim = s.get_timings()
+        c1 = s.get_counters()
+        k1, w1 = s.energy()
+        st = s.get_particles(0, N)
+        k = 4096 if w == "c2" else 2048
+        idx = inputs.sample_indices(N, k, seed + 1000).astype(np.int32)
+        s.predict(t_end)
+        a, j, p = s.compute_forces(idx)
+        s.close()
+        ar, jr, pr = oracle.forces(st["m"], st["x"], st["v"], eps, idx=idx.astype(np.int64), compensated=True)
+        out = {"workload": w, "N": N, "eps": eps, "t_end": t_end,
+               "precision": "fp64" if prec == nb.NB_FP64 else "mixed",
+               "interactions": tim["interactions"], "wall_s": wall,
+               "interactions_per_s": tim["interactions"] / wall,
+               "gflops_60": tim["interactions"] / wall * FLOP_PER_INTERACTION / 1e9,
+               "block_steps": c1["block_steps"] - c0["block_steps"],
+               "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0),
+               "final_state_forces_vs_oracle": {
+                   "sample": k, "acc_median": float(np.median(rel(a, ar))), "acc_max": float(rel(a, ar).max()),
+                   "jerk_median": float(np.median(rel(j, jr))), "jerk_max": float(rel(j, jr).max()),
+                   "pot_max": float((np.abs(p - pr) / np.abs(pr)).max())}}
+        if w == "c5":
+            out["wall_per_nbody_time_unit_s_extrapolated"] = wall / t_end
+        print(json.dumps(out), flush=True)
+        return
+
+    if w == "c4":
+        sizes = inputs.ensemble_sizes(512, 256, 16384, seed=7)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        eps = 1.0 / (4.0 * sizes.astype(np.float64) ** (1.0 / 3.0))
+        parts = [inputs.plummer(int(n), 10000 + q, "salpeter") for q, n in enumerate(sizes)]
+        m = np.concatenate([p[0] for p in parts])
+        x = np.concatenate([p[1] for p in parts])
+        v = np.concatenate([p[2] for p in parts])
+        t_end = 1.0 / 16
+        res = {}
+        finals = {}
+        for mode, name in ((nb.NB_ENSEMBLE_PERSISTENT, "persistent_graph"),
+                           (nb.NB_ENSEMBLE_PER_CLUSTER, "per_cluster_launches")):
+            e = nb.Ensemble(off, eps, nb.NB_MIXED, 0)
+            e.set_params(0.01, 0.01, 2.0 ** -22, t_end)
+            e.set_j_particles(0, m, x, v)
+            e.initial_forces_and_dt()
+            if name == "persistent_graph":
+                ek0, ep0 = e.energy()
+            e.get_timings(reset=True)
+            c0 = e.get_counters()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e.integrate(t_end, mode)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            tim = e.get_timings()
+            c1 = e.get_counters()
+            if name == "persistent_graph":
+                ek1, ep1 = e.energy()
+            finals[name] = e.get_particles(0, int(off[-1]))
+            e.close()
+            res[name] = {"wall_s": wall, "interactions": tim["interactions"],
+                         "interactions_per_s": tim["interactions"] / wall,
+                         "kernel_launches": c1["kernel_launches"] - c0["kernel_launches"],
+                         "block_steps": c1["block_steps"] - c0["block_steps"]}
+        drift = np.abs((ek1 + ep1) - (ek0 + ep0)) / np.abs(ek0 + ep0)
+        # oracle: 16 seeded clusters with N_c <= 4096 integrated fully, energy drift compared
+        small = np.nonzero(sizes <= 4096)[0]
+        pick = np.sort(np.random.default_rng(77).choice(small, 16, replace=False))
+        orc = []
+        for q in pick:
+            a, b = off[q], off[q + 1]
+            r = oracle.hermite_run(m[a:b], x[a:b], v[a:b], eps[q], 0.01, 2.0 ** -22, t_end, t_end)
+            E0 = sum(oracle.energy(m[a:b], x[a:b], v[a:b], eps[q]))
+            d_orc = abs(sum(oracle.energy(m[a:b], r["x"], r["v"], eps[q])) - E0) / abs(E0)
+            fx = finals["persistent_graph"]
+            d_gpu = abs(sum(oracle.energy(m[a:b], fx["x"][a:b], fx["v"][a:b], eps[q])) - E0) / abs(E0)
+            orc.append({"cluster": int(q), "N": int(b - a), "drift_gpu": d_gpu, "drift_oracle": d_orc})
+        dx = np.abs(finals["persistent_graph"]["x"] - finals["per_cluster_launches"]["x"]).max()
+        print(json.dumps({"workload": "c4", "clusters": 512, "N_total": int(off[-1]), "t_end": t_end,
+                          "modes": res,
+                          "speedup_persistent_vs_per_cluster": res["per_cluster_launches"]["wall_s"] /
+                          res["persistent_graph"]["wall_s"],
+                          "max_abs_dx_between_modes": float(dx),
+                          "energy_drift_gpu_median": float(np.median(drift)),
+                          "energy_drift_gpu_max": float(drift.max()),
+                          "oracle_subset": orc,
+                          "oracle_subset_within_2x": all(o["drift_gpu"] <= 2 * o["drift_oracle"] + 1e-9 for o in orc)}),
+              flush=True)
+        return
+    raise SystemExit(f"unknown workload {w}")
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload != "c3":
+        run_integration(args)
         return
 
     import torch
@@ -210,14 +343,19 @@ def main():
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         flush.fill_(1.0)
+        step_ev[k].record(stream)
         s.step()
+    step_ev[args.steps].record(stream)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    per_step = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
+    print(f"per-step ms (flush excluded after the first): {[round(x, 1) for x in per_step]}", file=sys.stderr)
     tim = s.get_timings()
     launches = s.get_counters()["kernel_launches"] - launches0
     t_max = ms
@@ -281,8 +419,12 @@ def main():
         torch.cuda.synchronize(dev)
         fp64_rate = float(k) * N / (e0.elapsed_time(e1) / 1e3)
         s.set_precision(prec)
+        pk = s.measure_peaks()
+        # the FP64 item issues 32 FP64-pipe instructions per interaction (source count)
         extra["fp64_gpu_path"] = {"value": fp64_rate, "unit": UNIT,
-                                  "sample": f"{k} active x N={N}", "vs_mixed": fp64_rate / value * ws}
+                                  "sample": f"{k} active x N={N}", "vs_mixed": fp64_rate / value * ws,
+                                  "fp64_pipe_frac": fp64_rate * 32 / (pk["fp64_tflops"] * 1e12 / 2)}
+        extra["peaks_measured"] = pk
         if not args.no_cpu:
             import oracle
             oracle.build()

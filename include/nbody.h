@@ -62,7 +62,8 @@ typedef struct nb_ctx nb_ctx;   /* opaque, owned by the library */
 /*
  * nb_create -- make a context for up to n_max particles on CUDA device
  * `device`, working on `cuda_stream` (a cudaStream_t; NULL = a stream the
- * library creates and owns).  precision: NB_FP64 or NB_MIXED (changeable
+ * library creates and owns; pass cudaStreamLegacy to work on the legacy
+ * default stream).  precision: NB_FP64 or NB_MIXED (changeable
  * with nb_set_precision).  Allocates all device memory the context needs up
  * front (about 0.3 KB per particle).  Parameters start at the paper's values
  * (Sec. 2): eps = 2^-8, dt in [2^-22, 2^-3], eta = 0.01.
@@ -236,6 +237,14 @@ int nb_set_tuning(nb_ctx* ctx, int i_per_thread, int threads, int j_tile, int n_
  * (any pointer may be NULL).
  */
 int nb_autotune(nb_ctx* ctx, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split);
+
+/*
+ * nb_measure_peaks -- measured arithmetic throughput of the context's GPU:
+ * dependent FMA chains in FP32 and FP64 (TFLOP/s, 2 flop per FMA) and the
+ * hardware rsqrt (T results/s).  Roofline denominators for the force paths
+ * (not in the paper).  Uses the context's scratch; any pointer may be NULL.
+ */
+int nb_measure_peaks(nb_ctx* ctx, double* fp32_tflops, double* fp64_tflops, double* rsqrt_tops);
 
 /* ---- batched ensemble of independent clusters --------------------------- */
 /*

@@ -753,18 +753,26 @@ cudaError_t build_graph(nb_ctx* c, Batch* b) {
   np.conditional.size = 1;
   cudaGraphNode_t node;
   if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  // capture on a private stream (the context's stream may be the legacy
+  // default stream, which cannot be captured); the graph runs on c->stream
+  cudaStream_t cap = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       const int64_t launches = c->launches;
+      cudaStream_t own = c->stream;
+      c->stream = cap;
       cudaError_t ec = capture_step(c, b, h, 1);
+      c->stream = own;
       c->launches = launches;
       cudaGraph_t got = nullptr;
-      e = cudaStreamEndCapture(c->stream, &got);
+      e = cudaStreamEndCapture(cap, &got);
       if (ec != cudaSuccess) e = ec;
     }
   }
+  if (cap) cudaStreamDestroy(cap);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
   cudaGraphDestroy(g);
   if (e == cudaSuccess) b->exec_precision = c->precision;

@@ -43,6 +43,20 @@
 #ifndef NB_MIXED_NEWTON
 #define NB_MIXED_NEWTON 0
 #endif
+// FP64 accumulators of the mixed path in shared memory instead of registers
+#ifndef NB_MIXED_SMEM_ACC
+#define NB_MIXED_SMEM_ACC 0
+#endif
+// double-single (FP32 TwoSum) accumulators instead of FP64 in the mixed path
+#ifndef NB_MIXED_DS_FOLD
+#define NB_MIXED_DS_FOLD 0
+#endif
+// unroll depth of the mixed inner loop over a j-tile
+#ifndef NB_MIXED_UNROLL
+#define NB_MIXED_UNROLL 4
+#endif
+#define NB_STR_(x) #x
+#define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR_(unroll n))
 
 namespace nbk {
 
@@ -86,7 +100,7 @@ __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, c
                                                 const float2* __restrict__ sC, const float (&xh)[IPT][3],
                                                 const float (&xl)[IPT][3], const float (&vi)[IPT][3],
                                                 const int (&rel)[IPT], float eps2, float (&p)[IPT][7]) {
-#pragma unroll 4
+  NB_PRAGMA_UNROLL(NB_MIXED_UNROLL)
   for (int q = 0; q < JT; ++q) {
     const float4 A = sA[q];
     const float4 B = sB[q];
@@ -140,7 +154,34 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
   const int tid = threadIdx.x;
   float xh[IPT][3], xl[IPT][3], vi[IPT][3];
   int64_t self[IPT];
+#if NB_MIXED_DS_FOLD
+  // double-single accumulators: the per-tile FP32 partial is added with
+  // Knuth's TwoSum in FP32 (no FP64 instruction in the loop at all)
+  float acc_hi[IPT][7], acc_lo[IPT][7];
+#elif NB_MIXED_SMEM_ACC
+  // FP64 accumulators in shared memory: fewer registers, more resident warps
+  __shared__ double s_acc[IPT * 7 * NT];
+#define NB_ACC(k, c) s_acc[((k) * 7 + (c)) * NT + tid]
+#else
   double acc[IPT][7];
+#define NB_ACC(k, c) acc[k][c]
+#endif
+#if NB_MIXED_DS_FOLD
+#define NB_ACC_ZERO(k, c) (acc_hi[k][c] = acc_lo[k][c] = 0.0f)
+#define NB_ACC_ADD(k, c, val)                                   \
+  do {                                                          \
+    const float a_ = acc_hi[k][c], b_ = (val);                  \
+    const float s_ = a_ + b_;                                   \
+    const float bb_ = s_ - a_;                                  \
+    acc_lo[k][c] += (a_ - (s_ - bb_)) + (b_ - bb_);             \
+    acc_hi[k][c] = s_;                                          \
+  } while (0)
+#define NB_ACC_GET(k, c) ((double)acc_hi[k][c] + (double)acc_lo[k][c])
+#else
+#define NB_ACC_ZERO(k, c) (NB_ACC(k, c) = 0.0)
+#define NB_ACC_ADD(k, c, val) (NB_ACC(k, c) += (double)(val))
+#define NB_ACC_GET(k, c) NB_ACC(k, c)
+#endif
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     int64_t pos = ibase + k * NT + tid;
@@ -154,7 +195,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     xl[k][0] = B.x; xl[k][1] = B.y; xl[k][2] = B.z;
     vi[k][0] = B.w; vi[k][1] = C.x; vi[k][2] = C.y;
 #pragma unroll
-    for (int c = 0; c < 7; ++c) acc[k][c] = 0.0;
+    for (int c = 0; c < 7; ++c) NB_ACC_ZERO(k, c);
   }
 
   const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
@@ -197,7 +238,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 #pragma unroll
     for (int k = 0; k < IPT; ++k)
 #pragma unroll
-      for (int c = 0; c < 7; ++c) acc[k][c] += (double)p[k][c];
+      for (int c = 0; c < 7; ++c) NB_ACC_ADD(k, c, p[k][c]);
     __syncthreads();
   }
   cp_async_wait<0>();
@@ -207,9 +248,13 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     const int64_t pos = ibase + k * NT + tid;
     if (pos >= n) continue;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) out[c * ostride + pos] = acc[k][c];
-    out[6 * ostride + pos] = finalize ? -acc[k][6] : acc[k][6];
+    for (int c = 0; c < 6; ++c) out[c * ostride + pos] = NB_ACC_GET(k, c);
+    out[6 * ostride + pos] = finalize ? -NB_ACC_GET(k, 6) : NB_ACC_GET(k, 6);
   }
+#undef NB_ACC
+#undef NB_ACC_ZERO
+#undef NB_ACC_ADD
+#undef NB_ACC_GET
 }
 
 template <int JT>

@@ -29,7 +29,7 @@ EXPORTS = (
     "nb_set_j_particles", "nb_set_n", "nb_get_n", "nb_get_particles", "nb_next_block", "nb_predict",
     "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_last_error", "nb_clear_error",
-    "nb_set_tuning", "nb_autotune", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
+    "nb_set_tuning", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
 
@@ -86,6 +86,7 @@ def lib():
         "nb_set_tuning": (_int, [_vp, _int, _int, _int, _int]),
         "nb_autotune": (_int, [_vp, _i64, _pint, _pint, _pint, _pint]),
         "nb_ensemble_create": (_int, [ctypes.POINTER(_vp), _i32, _vp, _vp, _int, _int, _vp]),
+        "nb_measure_peaks": (_int, [_vp, _pd, _pd, _pd]),
         "nb_ensemble_initial_forces_and_dt": (_int, [_vp]),
         "nb_ensemble_integrate": (_int, [_vp, _d, _int]),
         "nb_ensemble_energy": (_int, [_vp, _vp, _vp]),
@@ -129,6 +130,19 @@ def _kind_ptr(a, dtype):
     return NB_PTR_HOST, ctypes.c_void_p(arr.ctypes.data), arr
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def _stream(stream):
+    """cudaStream_t for a torch stream / raw handle; torch's default stream
+    (handle 0) is passed as cudaStreamLegacy because NULL asks the library
+    for a stream of its own."""
+    if stream is None:
+        return None
+    h = int(getattr(stream, "cuda_stream", stream))
+    return _vp(h if h != 0 else CUDA_STREAM_LEGACY)
+
+
 def _marshal(arrays, dtypes):
     kinds, ptrs, keep = set(), [], []
     for a, dt in zip(arrays, dtypes):
@@ -159,7 +173,7 @@ def nb_default_params():
 
 def nb_create(n_max, precision=NB_MIXED, device=0, stream=None):
     h = _vp()
-    s = None if stream is None else _vp(int(getattr(stream, "cuda_stream", stream)))
+    s = _stream(stream)
     _check(lib().nb_create(ctypes.byref(h), int(n_max), int(precision), int(device), s), "nb_create")
     return h
 
@@ -303,11 +317,17 @@ def nb_autotune(ctx, n):
     return dict(i_per_thread=v[0].value, threads=v[1].value, j_tile=v[2].value, n_split=v[3].value)
 
 
+def nb_measure_peaks(ctx):
+    v = [_d() for _ in range(3)]
+    _check(lib().nb_measure_peaks(ctx, *[ctypes.byref(x) for x in v]), "nb_measure_peaks")
+    return dict(fp32_tflops=v[0].value, fp64_tflops=v[1].value, rsqrt_tops=v[2].value)
+
+
 def nb_ensemble_create(offsets, eps, precision=NB_MIXED, device=0, stream=None):
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     eps = np.ascontiguousarray(eps, dtype=np.float64)
     h = _vp()
-    s = None if stream is None else _vp(int(getattr(stream, "cuda_stream", stream)))
+    s = _stream(stream)
     _check(lib().nb_ensemble_create(ctypes.byref(h), int(offsets.shape[0] - 1), offsets.ctypes.data_as(_vp),
                                     eps.ctypes.data_as(_vp), int(precision), int(device), s),
            "nb_ensemble_create")
@@ -341,7 +361,7 @@ def nb_forces_fp64_noalloc(m, x, v, eps, i_idx, acc=None, jerk=None, pot=None, s
                              [np.float64, np.float64, np.float64, np.int32, np.float64, np.float64, np.float64])
     if kind != NB_PTR_DEVICE:
         raise TypeError("nb_forces_fp64_noalloc takes device (CUDA) tensors only")
-    s = None if stream is None else _vp(int(getattr(stream, "cuda_stream", stream)))
+    s = _stream(stream)
     _check(lib().nb_forces_fp64_noalloc(int(m.shape[0]), p[0], p[1], p[2], float(eps), p[3], n, p[4], p[5],
                                         p[6], s), "nb_forces_fp64_noalloc")
 
