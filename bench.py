@@ -70,6 +70,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device="cpu"):
+    """The largest value of x over all ranks (x itself with one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, t_max_s):
+    """Units processed by all replicas divided by the slowest rank's time."""
+    return float(units_per_rank) * ws / t_max_s
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -358,13 +373,9 @@ def main():
     print(f"per-step ms (flush excluded after the first): {[round(x, 1) for x in per_step]}", file=sys.stderr)
     tim = s.get_timings()
     launches = s.get_counters()["kernel_launches"] - launches0
-    t_max = ms
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms, ws, dev)
     inter_rank = float(N) * N * args.steps
-    value = inter_rank * ws / (t_max / 1e3)
+    value = whole_job_rate(inter_rank, ws, t_max / 1e3)
 
     # roofline of the force kernel (events on the context's stream around each launch)
     force_s_per_launch = tim["ms_force"] / 1e3 / args.steps
@@ -389,11 +400,7 @@ def main():
             s.step()
             s.get_particles(0, N, out=hout)
         barrier()
-        e_s = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([e_s], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_s = float(tt.item())
+        e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
         bi = sum(t.numel() * 8 for t in hin.values())
         bo = sum(t.numel() * 8 for t in hout.values())
         e2e = {"value": float(N) * N * e_steps * ws / e_s, "unit": UNIT, "h2d_bytes_per_step": bi,

@@ -61,7 +61,8 @@ void free_ctx(nb_ctx* c) {
   if (!c) return;
   void* dptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->jA, c->jB,
                    c->jC, c->F, c->part, c->act, c->ident, c->ulist, c->sel_min, c->sel_cnt, c->red,
-                   c->status, c->d_offsets, c->d_ceps};
+                   c->status, c->d_offsets, c->d_ceps, c->perm, c->iperm, c->skey[0], c->skey[1],
+                   c->sval[0], c->sval[1], c->shist, c->tbox};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -98,13 +99,8 @@ nb_tuning pick_tuning(const nb_ctx* c, int64_t n) {
     const nb_tune_entry& e = c->tune_table[i];
     if (n >= e.n_lo && n < e.n_hi && nb_tuning_supported(c->precision, e.cfg)) return e.cfg;
   }
-  nb_tuning t = nb_default_tuning(c->precision);
-  if (c->precision == NB_MIXED) {
-    // small active blocks: fewer i per CTA so that the split-j grid stays full
-    if (n <= 2048) t.ipt = 1;
-    else if (n <= 32768) t.ipt = 2;
-  }
-  return t;
+  (void)n;
+  return nb_default_tuning(c->precision);
 }
 
 // device view of a caller's list (copied to ulist for host lists)
@@ -168,8 +164,22 @@ int get_scalar(nb_ctx* c, const double* src, double* dst, int64_t count, int ptr
   return NB_OK;
 }
 
+// (re)compute the spatial order of the j-store when the particles changed or
+// after sort_interval block steps; the next prediction writes that order
+int ensure_sorted(nb_ctx* c) {
+  if (c->n_clusters > 0 || c->n <= 0) return NB_OK;
+  if (c->perm_valid && c->perm_age < c->sort_interval) return NB_OK;
+  NB_CUDA(c, nb_spatial_sort(c));
+  c->perm_valid = true;
+  c->perm_age = 0;
+  c->pred_valid = false;
+  return NB_OK;
+}
+
 // block selection with the result copied to host: t_next, n
 int select_block(nb_ctx* c, double* t_next, int64_t* n) {
+  int rs = ensure_sorted(c);
+  if (rs) return rs;
   NB_CUDA(c, nb_launch_select(c));
   unsigned char* h = (unsigned char*)c->hpin;
   NB_CUDA(c, cudaMemcpyAsync(h, c->sel_min + c->sel_ctas, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -209,6 +219,7 @@ int step_after_select(nb_ctx* c, double t, int64_t n) {
   c->f_valid = false;
   c->ev_pending = true;
   c->steps += 1;
+  c->perm_age += 1;
   return NB_OK;
 }
 
@@ -284,6 +295,7 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
   c->n_max = n_max;
   c->n_pad = ((n_max + NB_JPAD - 1) / NB_JPAD) * NB_JPAD;
   c->sel_ctas = 1024;
+  c->sort_interval = 64;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = sms > 0 ? sms : 1;
@@ -304,7 +316,10 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
   NB_ALLOC(c->jC, np) NB_ALLOC(c->F, 7 * np) NB_ALLOC(c->part, (size_t)c->part_elems)
   NB_ALLOC(c->act, np) NB_ALLOC(c->ident, np) NB_ALLOC(c->ulist, np)
   NB_ALLOC(c->sel_min, (size_t)c->sel_ctas + 1) NB_ALLOC(c->sel_cnt, (size_t)c->sel_ctas + 1)
-  NB_ALLOC(c->red, 2 * 1024 + 8) NB_ALLOC(c->status, 1)
+  NB_ALLOC(c->red, NB_RED_DOUBLES) NB_ALLOC(c->status, 1)
+  NB_ALLOC(c->perm, np) NB_ALLOC(c->iperm, np) NB_ALLOC(c->skey[0], np) NB_ALLOC(c->skey[1], np)
+  NB_ALLOC(c->sval[0], np) NB_ALLOC(c->sval[1], np) NB_ALLOC(c->shist, (np / 2048 + 1) * 256)
+  NB_ALLOC(c->tbox, 2 * (np / NB_BOX_TILE + 1))
 #undef NB_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost(&c->hpin, kPinnedBytes);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -383,6 +398,7 @@ int nb_set_j_particles(nb_ctx* c, int64_t first, int64_t count, const double* m,
   if ((r = put_scalar(c, dt, c->dt, first, count, ptr_kind))) return r;
   if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
   if (first + count > c->n) c->n = first + count;
+  c->perm_valid = false;
   c->pred_valid = false;
   c->f_valid = false;
   return NB_OK;
@@ -394,6 +410,7 @@ int nb_set_n(nb_ctx* c, int64_t n) {
   c->n = n;
   c->pred_valid = false;
   c->f_valid = false;
+  c->perm_valid = false;
   return NB_OK;
 }
 
@@ -437,6 +454,8 @@ int nb_next_block(nb_ctx* c, double* t_next, int32_t* active_idx, int64_t* n_act
     NB_CUDA(c, cudaMemcpyAsync(active_idx, c->act, *n_active * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the device list is in the j-store's spatial order; the caller gets ascending indices
+    std::sort(active_idx, active_idx + *n_active);
   }
   return NB_OK;
 }
@@ -445,6 +464,8 @@ int nb_predict(nb_ctx* c, double t) {
   NB_SINGLE(c);
   if (c->n <= 0) return fail(c, NB_ESTATE);
   if (!isfinite(t)) return fail(c, NB_EINVAL);
+  int rs = ensure_sorted(c);
+  if (rs) return rs;
   NB_CUDA(c, nb_launch_predict(c, t, false));
   c->t_pred = t;
   c->pred_valid = true;
@@ -504,6 +525,10 @@ int nb_initial_forces_and_dt(nb_ctx* c) {
     return r == NB_OK ? r : fail(c, r);
   }
   if (c->n <= 0) return fail(c, NB_ESTATE);
+  {
+    int rs = ensure_sorted(c);
+    if (rs) return rs;
+  }
   NB_CUDA(c, nb_launch_predict(c, 0.0, true));
   NB_CUDA(c, nb_forces(c, c->ident, c->n));
   NB_CUDA(c, nb_launch_initial_dt(c));
@@ -562,6 +587,10 @@ int nb_integrate(nb_ctx* c, double t_end, int use_graph) {
 int nb_energy(nb_ctx* c, double* ekin, double* epot) {
   NB_SINGLE(c);
   if (c->n <= 0) return fail(c, NB_ESTATE);
+  {
+    int rs = ensure_sorted(c);
+    if (rs) return rs;
+  }
   NB_CUDA(c, nb_launch_predict(c, 0.0, true));
   NB_CUDA(c, nb_forces(c, c->ident, c->n));
   double* d_out = c->red + 2 * 1024;

@@ -27,7 +27,7 @@
 namespace {
 
 constexpr int kSelChunk = 2048;   // particles per selection chunk (chunks never straddle clusters)
-constexpr int kMixNT = 128, kMixIPT = 2, kMixJT = 128;   // batched mixed item shape
+constexpr int kMixNT = 128, kMixIPT = 1, kMixJT = 128;   // batched mixed item shape
 constexpr int kF64NT = 128, kF64JT = 64;                 // batched FP64 item shape
 constexpr int64_t kMaxIters = 50000000;                  // hard cap on loop iterations
 
@@ -964,6 +964,7 @@ int nb_ensemble_integrate(nb_ctx* c, double t_end, int mode) {
     if (copy_state(ch, 0, c, o, n, c->stream) != cudaSuccess) return NB_ECUDA;
     ch->n = n;
     ch->pred_valid = ch->f_valid = false;
+    ch->perm_valid = false;
     int r = nb_set_params(ch, c->h_ceps[q], c->eta, c->dt_min, c->dt_max);
     if (r == NB_OK) r = nb_integrate(ch, t_end, 0);
     if (r != NB_OK) return r;

@@ -95,7 +95,15 @@ __device__ __forceinline__ void mixed_load_tile(float4* sA, float4* sB, float2* 
 }
 
 // One j-tile against the thread's IPT i-particles; FP32 partials in p.
-template <int IPT, int JT, bool MASK>
+// MODE: kFar  -- the tile is far from every i of the warp: hi parts alone
+//                (r = x_j.hi - x_i.hi, within 2^-24 (|x_i|+|x_j|) of the exact
+//                difference, i.e. FP32 accuracy at the far-test distance);
+//       kNear -- double-single difference;
+//       kSelf -- double-single difference, pairs with j == i get 1/s = 0.
+constexpr int kFar = 0, kNear = 1, kSelf = 2;
+constexpr float kFarTheta = 0.25f;  // far test: box gap >= theta * (|x|max_i + |x|max_j)
+
+template <int IPT, int JT, int MODE>
 __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, const float4* __restrict__ sB,
                                                 const float2* __restrict__ sC, const float (&xh)[IPT][3],
                                                 const float (&xl)[IPT][3], const float (&vi)[IPT][3],
@@ -107,9 +115,9 @@ __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, c
     const float2 C = sC[q];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const float dx = (A.x - xh[k][0]) + (B.x - xl[k][0]);
-      const float dy = (A.y - xh[k][1]) + (B.y - xl[k][1]);
-      const float dz = (A.z - xh[k][2]) + (B.z - xl[k][2]);
+      const float dx = MODE == kFar ? A.x - xh[k][0] : (A.x - xh[k][0]) + (B.x - xl[k][0]);
+      const float dy = MODE == kFar ? A.y - xh[k][1] : (A.y - xh[k][1]) + (B.y - xl[k][1]);
+      const float dz = MODE == kFar ? A.z - xh[k][2] : (A.z - xh[k][2]) + (B.z - xl[k][2]);
       const float wx = B.w - vi[k][0];
       const float wy = C.x - vi[k][1];
       const float wz = C.y - vi[k][2];
@@ -123,7 +131,7 @@ __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, c
 #else
       float rinv = nb_rsqrt_approx(r2);
 #endif
-      if (MASK) rinv = (q == rel[k]) ? 0.0f : rinv;
+      if (MODE == kSelf) rinv = (q == rel[k]) ? 0.0f : rinv;
       const float rinv2 = rinv * rinv;
       const float mr = A.w * rinv;
       const float mr3 = mr * rinv2;
@@ -150,7 +158,11 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
                                            int64_t jlo, int64_t jhi, int64_t idx_hi,
                                            const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                            float eps2, double* __restrict__ out, int64_t ostride,
-                                           bool finalize) {
+                                           bool finalize, const int32_t* __restrict__ iperm = nullptr,
+                                           const float4* __restrict__ tbox = nullptr) {
+  // iperm (optional): j-store slot of each particle (spatial order); tbox
+  // (optional, JT == NB_BOX_TILE, tiles aligned to slot 0): per-tile boxes
+  // that allow the far-tile pass.
   const int tid = threadIdx.x;
   float xh[IPT][3], xl[IPT][3], vi[IPT][3];
   int64_t self[IPT];
@@ -188,7 +200,11 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     if (pos >= n) pos = n - 1;
     int64_t p = list[pos];
     p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
-    self[k] = p;
+    if (iperm) {
+      p = iperm[p];
+      p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);
+    }
+    self[k] = p;  // j-store slot of this i
     const float4 A = jA[p], B = jB[p];
     const float2 C = jC[p];
     xh[k][0] = A.x; xh[k][1] = A.y; xh[k][2] = A.z;
@@ -196,6 +212,29 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     vi[k][0] = B.w; vi[k][1] = C.x; vi[k][2] = C.y;
 #pragma unroll
     for (int c = 0; c < 7; ++c) NB_ACC_ZERO(k, c);
+  }
+  // box of the warp's i-particles (hi parts) and their largest |coordinate|
+  float wlo[3], whi[3], wr = 0.0f;
+  if (tbox) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      wlo[c] = xh[0][c];
+      whi[c] = xh[0][c];
+#pragma unroll
+      for (int k = 1; k < IPT; ++k) {
+        wlo[c] = fminf(wlo[c], xh[k][c]);
+        whi[c] = fmaxf(whi[c], xh[k][c]);
+      }
+      wr = fmaxf(wr, fmaxf(fabsf(wlo[c]), fabsf(whi[c])));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        wlo[c] = fminf(wlo[c], __shfl_xor_sync(0xffffffffu, wlo[c], o));
+        whi[c] = fmaxf(whi[c], __shfl_xor_sync(0xffffffffu, whi[c], o));
+      }
+      wr = fmaxf(wr, __shfl_xor_sync(0xffffffffu, wr, o));
+    }
   }
 
   const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
@@ -230,10 +269,24 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 #pragma unroll
       for (int c = 0; c < 7; ++c) p[k][c] = 0.0f;
 
+    // far test (warp-uniform): box gap >= theta (|x|max of warp + |x|max of
+    // tile) bounds the hi-only difference error by 2^-24 (1/theta + 1)
+    bool far = false;
+    if (tbox) {
+      const int64_t t = jt / JT;
+      const float4 blo = tbox[2 * t], bhi = tbox[2 * t + 1];
+      const float gx = fmaxf(0.0f, fmaxf(blo.x - whi[0], wlo[0] - bhi.x));
+      const float gy = fmaxf(0.0f, fmaxf(blo.y - whi[1], wlo[1] - bhi.y));
+      const float gz = fmaxf(0.0f, fmaxf(blo.z - whi[2], wlo[2] - bhi.z));
+      const float lim = kFarTheta * (wr + blo.w);
+      far = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
+    }
     if (__any_sync(0xffffffffu, hit))
-      mixed_tile_pass<IPT, JT, true>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+      mixed_tile_pass<IPT, JT, kSelf>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+    else if (__all_sync(0xffffffffu, far))
+      mixed_tile_pass<IPT, JT, kFar>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
     else
-      mixed_tile_pass<IPT, JT, false>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+      mixed_tile_pass<IPT, JT, kNear>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
 
 #pragma unroll
     for (int k = 0; k < IPT; ++k)

@@ -13,14 +13,15 @@ template <int NT, int IPT, int JT>
 __global__ void __launch_bounds__(NT) force_mixed_kernel(
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
     int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t j_per_split, float eps2,
-    double* __restrict__ out, int64_t ostride, int finalize) {
+    double* __restrict__ out, int64_t ostride, int finalize, const int32_t* __restrict__ iperm,
+    const float4* __restrict__ tbox) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   const int split = blockIdx.y;
   const int64_t jlo = (int64_t)split * j_per_split;
   const int64_t jhi = min(jlo + j_per_split, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * (NT * IPT),
-                               eps2, o, ostride, finalize != 0);
+                               eps2, o, ostride, finalize != 0, iperm, tbox);
 }
 
 template <int NT, int IPT, int JT>
@@ -40,8 +41,12 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit, floa
   double* out = fin ? c->F : c->part;
   if (!fin && (int64_t)nsplit * 7 * ostride > c->part_elems) return cudaErrorInvalidValue;
   c->launches += fin ? 1 : 2;
+  // spatial order: i slots through iperm; far-tile boxes when the tiles match
+  const int32_t* iperm = c->perm_valid ? c->iperm : nullptr;
+  const float4* tbox = (c->perm_valid && JT == NB_BOX_TILE) ? c->tbox : nullptr;
   force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n,
-                                                              j_per_split, eps2, out, ostride, fin ? 1 : 0);
+                                                              j_per_split, eps2, out, ostride, fin ? 1 : 0,
+                                                              iperm, tbox);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);

@@ -26,6 +26,9 @@
 
 #define NB_JPAD 1024          // j-store padding granule (max j-tile)
 #define NB_PAD_POS 1.0e15     // position of padding particles (m = 0)
+#define NB_BOX_TILE 128       // j-tile of the spatial boxes (the mixed default j-tile)
+#define NB_RED_DOUBLES (8192 + 16)  // reduction scratch: partials, energies, bounding box
+#define NB_BBOX_OFFSET 8192         // 6 doubles of the particles' bounding box
 
 // device status word bits
 #define NB_ST_NUMERIC 1u
@@ -82,7 +85,16 @@ struct nb_ctx {
   unsigned long long* sel_min;  // per-CTA minima [sel_ctas] + result at [sel_ctas]
   int32_t* sel_cnt;             // per-CTA counts [sel_ctas] + total at [sel_ctas]
   int sel_ctas;
-  double* red;                  // reduction scratch [2 * 1024]
+  double* red;                  // reduction scratch [NB_RED_DOUBLES]
+  // spatial (Morton) order of the mixed j-store (spatial.cu)
+  int32_t *perm, *iperm;        // perm[slot] = particle, iperm[particle] = slot
+  uint32_t* skey[2];            // radix-sort key buffers
+  int32_t* sval[2];             // radix-sort value buffers
+  int32_t* shist;               // radix-sort digit histograms
+  float4* tbox;                 // per j-tile box: (lo, rmax), (hi, 0)
+  bool perm_valid;              // perm describes the current particles
+  int perm_age;                 // block steps since the last sort
+  int sort_interval;            // re-sort after this many block steps
   // device status
   nb_dev_status* status;
   // pinned host staging for small results
@@ -135,6 +147,10 @@ int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg);
 
 // the force dispatcher (capi.cu): picks the tuning and precision path
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
+
+// spatial.cu
+cudaError_t nb_spatial_sort(nb_ctx* c);       // perm / iperm from the current positions
+cudaError_t nb_launch_tile_boxes(nb_ctx* c);  // tbox from the predicted (permuted) j-store
 
 // ensemble.cu
 void nb_ensemble_free(nb_ctx* c);

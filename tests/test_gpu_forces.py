@@ -171,3 +171,22 @@ def test_bad_lists_rejected(nbl):
         bad_x[5, 1] = np.nan
         with pytest.raises(nbl.NBodyError):
             s.set_j_particles(0, m, bad_x, v)
+
+
+def test_autotune_picks_a_supported_launch(nbl):
+    # the autotuner times the supported launches for (N, n) and keeps the fastest
+    N, eps, n = 20000, 1 / 512, 700
+    m, x, v = inputs.plummer(N, 61)
+    idx = inputs.sample_indices(N, n, 62)
+    ref = oracle.forces(m, x, v, eps, idx=idx, compensated=True)
+    for P in (nbl.NB_FP64, nbl.NB_MIXED):
+        with nbl.NBody(N, P, 0) as s:
+            s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+            s.set_j_particles(0, m, x, v)
+            s.predict(0.0)
+            cfg = s.autotune(n)
+            assert cfg["threads"] in (64, 128, 256) and cfg["n_split"] >= 1
+            assert cfg["i_per_thread"] in ((1,) if P == nbl.NB_FP64 else (1, 2, 4))
+            s.predict(0.0)
+            got = s.compute_forces(idx.astype(np.int32))
+        _check(P, nbl, got, ref)
