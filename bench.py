@@ -58,8 +58,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5"],
-                    help="c3 (default): the timed benchmark; c2/c4/c5: long integrations, one JSON line")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5", "tapp"],
+                    help="c3 (default): the timed benchmark; c2/c4/c5: long integrations; tapp: time per "
+                         "N-body time unit vs N and the per-task model; one JSON line each")
+    ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
     return ap.parse_args()
 
 
@@ -217,7 +219,9 @@ def run_integration(args):
         c0 = s.get_counters()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.integrate(t_end, use_graph=True)
+        # c2 (FP64, many small blocks): the CUDA-graph loop; c5 (mixed, large blocks): the
+        # host-driven loop, whose force launches use the spatial j-order
+        s.integrate(t_end, use_graph=(w == "c2"))
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         tim = s.get_timings()
@@ -306,6 +310,71 @@ def run_integration(args):
                           "oracle_subset": orc,
                           "oracle_subset_within_2x": all(o["drift_gpu"] <= 2 * o["drift_oracle"] + 1e-9 for o in orc)}),
               flush=True)
+        return
+    if w == "tapp":
+        # T_app for one N-body time unit vs N on one GB300 (the single-node curves of the paper's
+        # timing figures), the per-task time of one block step with the average block size
+        # n = 0.20 N^0.81 (Sec. 3.2 profile), and the Sec. 4.1 model T = sum(tau_pred N +
+        # tau_force n N + tau_corr n) recalibrated with GB300's tau's (Eqs. 1-4).
+        eps, eta = 2.0 ** -8, 0.01
+        out = []
+        sizes = [int(s) for s in args.tapp_sizes.split(",")]
+        for N in sizes:
+            m, x, v = inputs.plummer(N, 100 + N)
+            s = nb.NBody(N, nb.NB_MIXED, 0)
+            s.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
+            s.set_j_particles(0, m, x, v)
+            s.initial_forces_and_dt()
+            # one step of the Sec. 3.2 profile: n = 0.20 N^0.81 active particles
+            n = inputs.block_size(N)
+            idx = inputs.sample_indices(N, n, 7).astype(np.int32)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            dev_idx = torch.from_numpy(idx).cuda()
+            A = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+            J = torch.empty_like(A)
+            P = torch.empty(n, dtype=torch.float64, device="cuda")
+            prof = []
+            for rep in range(4):
+                torch.cuda.synchronize()
+                ev[0].record()
+                s.predict(0.0)
+                ev[1].record()
+                s.compute_forces(dev_idx, A, J, P)
+                ev[2].record()
+                s.correct(dev_idx, 2.0 ** -22)
+                ev[3].record()
+                torch.cuda.synchronize()
+                prof.append([ev[k].elapsed_time(ev[k + 1]) for k in range(3)])
+                s.set_j_particles(0, m, x, v)   # undo the correction
+                s.initial_forces_and_dt()
+            pr = np.median(np.array(prof[1:]), axis=0)
+            # one N-body time unit with block steps
+            s.get_timings(reset=True)
+            c0 = s.get_counters()
+            k0, w0 = s.energy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.integrate(1.0, use_graph=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            tim = s.get_timings()
+            c1 = s.get_counters()
+            k1, w1 = s.energy()
+            s.close()
+            steps = c1["block_steps"] - c0["block_steps"]
+            inter = tim["interactions"]
+            psteps = inter / N
+            tp, tf, tc = tim["ms_pred"] / 1e3, tim["ms_force"] / 1e3, tim["ms_corr"] / 1e3
+            out.append({"N": N, "profile_step": {"n": n, "ms_predict": pr[0], "ms_force": pr[1], "ms_correct": pr[2]},
+                        "T_app_s": wall, "block_steps": steps, "particle_steps": psteps, "interactions": inter,
+                        "interactions_per_s": inter / wall,
+                        "tau_pred_s": tp / (steps * N), "tau_force_s": tf / inter, "tau_corr_s": tc / psteps,
+                        "model_T_s": tp + tf + tc, "share_force": tf / wall, "share_pred": tp / wall,
+                        "share_corr": tc / wall, "share_host_and_select": 1 - (tp + tf + tc) / wall,
+                        "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)})
+            print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+        print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": "mixed",
+                          "grape_tau_force_s": 4.3e-10, "rows": out}), flush=True)
         return
     raise SystemExit(f"unknown workload {w}")
 

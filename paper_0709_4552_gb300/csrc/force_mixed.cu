@@ -9,8 +9,13 @@
 
 namespace {
 
+// minimum resident CTAs per SM requested from the register allocator (1 = no cap)
+#ifndef NB_MIXED_MINB
+#define NB_MIXED_MINB 1
+#endif
+
 template <int NT, int IPT, int JT>
-__global__ void __launch_bounds__(NT) force_mixed_kernel(
+__global__ void __launch_bounds__(NT, (IPT == 1 && NT == 128) ? NB_MIXED_MINB : 1) force_mixed_kernel(
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
     int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t j_per_split, float eps2,
     double* __restrict__ out, int64_t ostride, int finalize, const int32_t* __restrict__ iperm,
