@@ -248,7 +248,20 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
 // the force dispatcher used by every entry point
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
   const nb_tuning cfg = pick_tuning(c, n);
-  return c->precision == NB_FP64 ? nb_forces_fp64(c, d_list, n, cfg) : nb_forces_mixed(c, d_list, n, cfg);
+  if (c->precision == NB_FP64) return nb_forces_fp64(c, d_list, n, cfg);
+  // mixed path with a spatial order: visit the list in that order.  The
+  // block-selection list already is; the identity list is visited as perm;
+  // any other list is sorted by the slots of its particles.
+  const int32_t* ord = nullptr;
+  if (c->perm_valid && c->n_clusters == 0 && d_list != c->act) {
+    if (d_list == c->ident && n == c->n) {
+      ord = c->perm;
+    } else if (n >= 8192 && n * 16 >= c->n) {  // sparse lists give loose warps anyway
+      cudaError_t e = nb_list_order(c, d_list, n, &ord);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return nb_forces_mixed(c, d_list, n, cfg, ord);
 }
 
 extern "C" {

@@ -159,7 +159,10 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
                                            const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                            float eps2, double* __restrict__ out, int64_t ostride,
                                            bool finalize, const int32_t* __restrict__ iperm = nullptr,
-                                           const float4* __restrict__ tbox = nullptr) {
+                                           const float4* __restrict__ tbox = nullptr,
+                                           const int32_t* __restrict__ ord = nullptr) {
+  // ord (optional): the list positions in processing order (a caller's list
+  // visited in spatial order); results always go to the list positions.
   // iperm (optional): j-store slot of each particle (spatial order); tbox
   // (optional, JT == NB_BOX_TILE, tiles aligned to slot 0): per-tile boxes
   // that allow the far-tile pass.
@@ -198,6 +201,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
   for (int k = 0; k < IPT; ++k) {
     int64_t pos = ibase + k * NT + tid;
     if (pos >= n) pos = n - 1;
+    if (ord) pos = ord[pos];
     int64_t p = list[pos];
     p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
     if (iperm) {
@@ -298,8 +302,9 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
-    const int64_t pos = ibase + k * NT + tid;
+    int64_t pos = ibase + k * NT + tid;
     if (pos >= n) continue;
+    if (ord) pos = ord[pos];
 #pragma unroll
     for (int c = 0; c < 6; ++c) out[c * ostride + pos] = NB_ACC_GET(k, c);
     out[6 * ostride + pos] = finalize ? -NB_ACC_GET(k, 6) : NB_ACC_GET(k, 6);

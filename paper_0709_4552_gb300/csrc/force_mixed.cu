@@ -9,28 +9,34 @@
 
 namespace {
 
-// minimum resident CTAs per SM requested from the register allocator (1 = no cap)
+// minimum resident CTAs per SM asked of the register allocator for the
+// 128-thread, one-i-per-thread shape (0 = no request)
 #ifndef NB_MIXED_MINB
-#define NB_MIXED_MINB 1
+#define NB_MIXED_MINB 0
+#endif
+#if NB_MIXED_MINB > 0
+#define NB_MIXED_BOUNDS(NT, IPT) __launch_bounds__(NT, ((IPT) == 1 && (NT) == 128) ? NB_MIXED_MINB : 1)
+#else
+#define NB_MIXED_BOUNDS(NT, IPT) __launch_bounds__(NT)
 #endif
 
 template <int NT, int IPT, int JT>
-__global__ void __launch_bounds__(NT, (IPT == 1 && NT == 128) ? NB_MIXED_MINB : 1) force_mixed_kernel(
+__global__ void NB_MIXED_BOUNDS(NT, IPT) force_mixed_kernel(
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
     int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t j_per_split, float eps2,
     double* __restrict__ out, int64_t ostride, int finalize, const int32_t* __restrict__ iperm,
-    const float4* __restrict__ tbox) {
+    const float4* __restrict__ tbox, const int32_t* __restrict__ ord) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   const int split = blockIdx.y;
   const int64_t jlo = (int64_t)split * j_per_split;
   const int64_t jhi = min(jlo + j_per_split, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * (NT * IPT),
-                               eps2, o, ostride, finalize != 0, iperm, tbox);
+                               eps2, o, ostride, finalize != 0, iperm, tbox, ord);
 }
 
 template <int NT, int IPT, int JT>
-cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit, float eps2) {
+cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit, float eps2, const int32_t* ord) {
   const int64_t per_cta = (int64_t)NT * IPT;
   const int64_t itiles = (n + per_cta - 1) / per_cta;
   const int64_t n_j = ((c->n + JT - 1) / JT) * JT;  // padding particles (m = 0) fill the last tile
@@ -51,7 +57,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit, floa
   const float4* tbox = (c->perm_valid && JT == NB_BOX_TILE) ? c->tbox : nullptr;
   force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n,
                                                               j_per_split, eps2, out, ostride, fin ? 1 : 0,
-                                                              iperm, tbox);
+                                                              iperm, tbox, iperm ? ord : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
@@ -68,9 +74,10 @@ bool nb_mixed_supported(const nb_tuning& t) {
 
 #define NB_MIXED_CASE(NT_, IPT_, JT_)                            \
   if (cfg.threads == NT_ && cfg.ipt == IPT_ && cfg.jtile == JT_) \
-    return launch<NT_, IPT_, JT_>(c, d_list, n, nsplit, eps2);
+    return launch<NT_, IPT_, JT_>(c, d_list, n, nsplit, eps2, ord);
 
-cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg) {
+cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                            const int32_t* ord) {
   if (n <= 0) return cudaSuccess;
   const float eps2 = (float)(c->eps * c->eps);
   const int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg);

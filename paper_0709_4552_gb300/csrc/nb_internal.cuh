@@ -137,7 +137,9 @@ cudaError_t nb_launch_check_list(const int32_t* d_list, int64_t n, int64_t N, un
 // ---- launchers (force_fp64.cu / force_mixed.cu) ----------------------------
 // forces on the list d_list[0..n) from all N j; results to c->F
 cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
-cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
+// ord (optional): processing order of the list positions (spatial order)
+cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                            const int32_t* ord = nullptr);
 // split-j reduction (force_fp64.cu): part[S][7][n] -> F in fixed order, potential sign
 cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit,
                                    int64_t stride);
@@ -151,6 +153,8 @@ cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
 // spatial.cu
 cudaError_t nb_spatial_sort(nb_ctx* c);       // perm / iperm from the current positions
 cudaError_t nb_launch_tile_boxes(nb_ctx* c);  // tbox from the predicted (permuted) j-store
+// processing order of a caller's list in the spatial order (device array of n positions)
+cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord);
 
 // ensemble.cu
 void nb_ensemble_free(nb_ctx* c);

@@ -207,6 +207,34 @@ int grid_for(int64_t n, int threads, int cap) {
   return (int)g;
 }
 
+// keys: slot of each listed particle (clamped); values: list positions
+__global__ void list_keys(const int32_t* __restrict__ list, int64_t n, const int32_t* __restrict__ iperm,
+                          int64_t N, uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = list[k];
+    p = p < 0 ? 0 : (p >= N ? N - 1 : p);
+    key[k] = (uint32_t)iperm[p];
+    val[k] = (int32_t)k;
+  }
+}
+
+// stable LSD radix sort of (skey[0], sval[0])[0..n) on the low `bits` bits;
+// *cur = the buffer holding the result
+cudaError_t sort_pairs(nb_ctx* c, int64_t n, int bits, int* cur) {
+  const int nblocks = (int)((n + kSortChunk - 1) / kSortChunk);
+  int b = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_count<<<nblocks, kSortThreads, 0, c->stream>>>(c->skey[b], n, shift, c->shist, nblocks);
+    scan_exclusive<<<1, 1024, 0, c->stream>>>(c->shist, (int64_t)nblocks * kRadix);
+    radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(c->skey[b], c->sval[b], c->skey[b ^ 1], c->sval[b ^ 1],
+                                                           n, shift, c->shist, nblocks);
+    b ^= 1;
+    c->launches += 3;
+  }
+  *cur = b;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t nb_spatial_sort(nb_ctx* c) {
@@ -218,20 +246,30 @@ cudaError_t nb_spatial_sort(nb_ctx* c) {
   bbox_final<<<1, 32, 0, c->stream>>>(nbb, c->red, box);
   morton_keys<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->n_pad, c->x, box, c->skey[0],
                                                                          c->sval[0]);
-  const int nblocks = (int)((N + kSortChunk - 1) / kSortChunk);
   int cur = 0;
-  for (int shift = 0; shift < 32; shift += 8) {
-    radix_count<<<nblocks, kSortThreads, 0, c->stream>>>(c->skey[cur], N, shift, c->shist, nblocks);
-    scan_exclusive<<<1, 1024, 0, c->stream>>>(c->shist, (int64_t)nblocks * kRadix);
-    radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(c->skey[cur], c->sval[cur], c->skey[cur ^ 1],
-                                                           c->sval[cur ^ 1], N, shift, c->shist, nblocks);
-    cur ^= 1;
-  }
-  // after 4 passes the sorted values are back in buffer 0
-  cudaError_t e = cudaMemcpyAsync(c->perm, c->sval[cur], N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = sort_pairs(c, N, 30, &cur);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(c->perm, c->sval[cur], N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return e;
   invert_perm<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->perm, c->iperm);
-  c->launches += 4 + 3 * 4 + 1;
+  c->launches += 4;
+  return cudaGetLastError();
+}
+
+// Processing order of a caller's active list in the spatial order: list
+// positions sorted by the j-store slot of their particle (stable).  The
+// mixed kernel then forms warps of nearby particles; results still go to the
+// caller's positions.  Returns a device array of n positions.
+cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord) {
+  list_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(d_list, n, c->iperm, c->n, c->skey[0],
+                                                                       c->sval[0]);
+  int bits = 1;
+  while (bits < 31 && ((int64_t)1 << bits) < c->n) ++bits;
+  int cur = 0;
+  cudaError_t e = sort_pairs(c, n, bits, &cur);
+  if (e != cudaSuccess) return e;
+  c->launches += 1;
+  *ord = c->sval[cur];
   return cudaGetLastError();
 }
 
