@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5", "tapp"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5", "tapp", "c3sweep"],
                     help="c3 (default): the timed benchmark; c2/c4/c5: long integrations; tapp: time per "
                          "N-body time unit vs N and the per-task model; one JSON line each")
     ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
@@ -310,6 +310,51 @@ def run_integration(args):
                           "oracle_subset": orc,
                           "oracle_subset_within_2x": all(o["drift_gpu"] <= 2 * o["drift_oracle"] + 1e-9 for o in orc)}),
               flush=True)
+        return
+    if w == "c3sweep":
+        # configuration 3's active-block sweep: N = 2^20 equal masses, eps = 1/4096, the first n of
+        # a seeded shuffle; mixed vs FP64 GPU path rates, and both paths' errors vs the oracle on
+        # 1024 sampled active particles
+        N, eps = 1 << 20, 1.0 / 4096
+        m, x, v = inputs.plummer(N, 3)
+        res = []
+        for n in (256, 4096, 65536, N):
+            act = inputs.sample_indices(N, n, 1003).astype(np.int32)
+            pos = inputs.sample_indices(n, min(n, 1024), 2003)
+            ref = oracle.forces(m, x, v, eps, idx=act[pos].astype(np.int64))
+            row = {"n_active": n}
+            for prec, name in ((nb.NB_MIXED, "mixed"), (nb.NB_FP64, "fp64")):
+                if prec == nb.NB_FP64 and n > 65536:
+                    continue  # 1.1e12 FP64 interactions take over a minute; the sample covers accuracy
+                s = nb.NBody(N, prec, 0, stream=torch.cuda.current_stream())
+                s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+                s.set_j_particles(0, m, x, v)
+                s.predict(0.0)
+                d_act = torch.from_numpy(act).cuda()
+                A = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+                J = torch.empty_like(A)
+                P = torch.empty(n, dtype=torch.float64, device="cuda")
+                s.compute_forces(d_act, A, J, P)
+                reps = 3 if n * N < 1e11 else 1
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    s.compute_forces(d_act, A, J, P)
+                e1.record()
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3 / reps
+                pp = torch.from_numpy(pos).cuda()
+                a, j, p = A[pp].cpu().numpy(), J[pp].cpu().numpy(), P[pp].cpu().numpy()
+                s.close()
+                ea, ej, ep = rel(a, ref[0]), rel(j, ref[1]), np.abs(p - ref[2]) / np.abs(ref[2])
+                row[name] = {"ms": sec * 1e3, "interactions_per_s": float(n) * N / sec,
+                             "frac_fp32_peak_60flop": float(n) * N / sec * 60 / 80.548e12,
+                             "acc_median": float(np.median(ea)), "acc_max": float(ea.max()),
+                             "jerk_median": float(np.median(ej)), "jerk_max": float(ej.max()),
+                             "pot_max": float(ep.max())}
+            res.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        print(json.dumps({"workload": "c3sweep", "N": N, "eps": eps, "rows": res}), flush=True)
         return
     if w == "tapp":
         # T_app for one N-body time unit vs N on one GB300 (the single-node curves of the paper's
