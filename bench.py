@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=1.0 / 4096)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=4096, help="sampled i for the oracle legs")
+    ap.add_argument("--cpu-sample", type=int, default=16384,
+                    help="sampled i for the oracle legs (the reference arm takes a quarter per step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
@@ -144,6 +145,15 @@ class ClockSampler:
 
 def fp32_peak_tflops(sms, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measured_hbm_gbs():
+    """The measured copy bandwidth of this GPU model (MEASURED_PEAKS.json at the repo root)."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # the fallback figure of an earlier GB300 measurement
 
 
 def run_reference(args, ws, rank):
@@ -318,7 +328,7 @@ def run_integration(args):
         N, eps = 1 << 20, 1.0 / 4096
         m, x, v = inputs.plummer(N, 3)
         res = []
-        for n in (256, 4096, 65536, N):
+        for n in (256, 4096, inputs.block_size(N), 65536, N):
             act = inputs.sample_indices(N, n, 1003).astype(np.int32)
             pos = inputs.sample_indices(n, min(n, 1024), 2003)
             ref = oracle.forces(m, x, v, eps, idx=act[pos].astype(np.int64))
@@ -494,8 +504,23 @@ def main():
     # roofline of the force kernel (events on the context's stream around each launch)
     force_s_per_launch = tim["ms_force"] / 1e3 / args.steps
     achieved_tflops = FLOP_PER_INTERACTION * float(N) * N / force_s_per_launch / 1e12
-    peak = fp32_peak_tflops(sms, SM_MAX_MHZ_FALLBACK)
+    # the FP64 path is bound by the FP64 pipe: 1/64 of the FP32 lanes on this part
+    fp_div = 1.0 if prec == nb.NB_MIXED else 64.0
+    peak = fp32_peak_tflops(sms, SM_MAX_MHZ_FALLBACK) / fp_div
     sm_mhz = clk["sm_mhz"] if clk else None
+    # predictor and corrector: HBM-bound passes, algorithmic bytes per particle
+    # (predictor: m, t, x, v, a, jerk read, FP64 xp, vp written, plus slot index and
+    # the 40 B mixed j-store; corrector: list, t, dt, a, jerk, 7 force rows, xp, vp
+    # read, x, v, a, jerk, pot, t, dt written)
+    pred_bytes = float(N) * (112 + 48 + (44 if prec == nb.NB_MIXED else 0))
+    corr_bytes = float(N) * 292
+    hbm = measured_hbm_gbs()
+    phases = {}
+    for name, key, b in (("predict", "ms_pred", pred_bytes), ("correct", "ms_corr", corr_bytes)):
+        ms_k = tim[key] / args.steps
+        gbs = b / (ms_k / 1e3) / 1e9 if ms_k > 0 else None
+        phases[name] = {"ms": ms_k, "bytes": b, "achieved_gbs": gbs, "peak_gbs": hbm,
+                        "frac": (gbs / hbm) if (gbs and hbm) else None}
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs,
     # the step, D2H of its results, all inside the timed region
@@ -580,8 +605,11 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak, "traffic": None,
                          "kernel": "force_mixed_kernel" if prec == nb.NB_MIXED else "force_fp64_kernel",
-                         "peak_basis": f"FP32 CUDA cores: {sms} SMs x 128 x 2 flop x {SM_MAX_MHZ_FALLBACK:.0f} MHz",
-                         "frac_at_sampled_clock": (achieved_tflops / fp32_peak_tflops(sms, sm_mhz)) if sm_mhz else None},
+                         "peak_basis": (f"FP32 CUDA cores: {sms} SMs x 128 x 2 flop x {SM_MAX_MHZ_FALLBACK:.0f} MHz"
+                                        + ("" if fp_div == 1.0 else " / 64 (FP64 pipe)")),
+                         "frac_at_sampled_clock": (achieved_tflops * fp_div / fp32_peak_tflops(sms, sm_mhz))
+                         if sm_mhz else None},
+            "hbm_rooflines": phases,
             "phases_ms_per_step": {"predict": tim["ms_pred"] / args.steps, "force": tim["ms_force"] / args.steps,
                                    "correct": tim["ms_corr"] / args.steps},
             "gpu_launches": int(launches) * ws,

@@ -55,6 +55,11 @@
 #ifndef NB_MIXED_UNROLL
 #define NB_MIXED_UNROLL 4
 #endif
+// one i per thread: two j per instruction with the packed FP32x2 operations
+// of sm_100+ (1 = on; 0 = the scalar loop)
+#ifndef NB_MIXED_PACKED
+#define NB_MIXED_PACKED 1
+#endif
 #define NB_STR_(x) #x
 #define NB_PRAGMA_UNROLL(n) _Pragma(NB_STR_(unroll n))
 
@@ -69,6 +74,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -91,6 +100,47 @@ __device__ __forceinline__ void mixed_load_tile(float4* sA, float4* sB, float2* 
     cp_async16(&sA[q], &jA[j]);
     cp_async16(&sB[q], &jB[j]);
     cp_async8(&sC[q], &jC[j]);
+  }
+}
+
+// Pair layout of one tile buffer for the packed loop: j-particles 2u and
+// 2u+1 side by side, so that one 16-byte broadcast yields two (j, j+1) pairs:
+//   P0[u] = (xh, xh', yh, yh')   P1[u] = (zh, zh', m, m')   (in sA)
+//   P2[u] = (vx, vx', vy, vy')   P3[u] = (vz, vz', xl, xl') (in sB)
+//   P4[u] = (yl, yl', zl, zl')                              (in sC)
+// (u < JT/2; same 40 B per particle as the plain layout).  The float of
+// particle q, pair slot (q & 1), sits at 4 (q >> 1) + (q & 1) (+2 for the
+// second pair of a vector); 4-byte asynchronous copies scatter it there.
+template <int JT>
+struct PairTile {
+  float *p0, *p1, *p2, *p3, *p4;
+  __device__ __forceinline__ PairTile(float4* sA, float4* sB, float2* sC)
+      : p0((float*)sA), p1((float*)(sA + JT / 2)), p2((float*)sB), p3((float*)(sB + JT / 2)), p4((float*)sC) {}
+};
+
+template <int NT, int JT>
+__device__ __forceinline__ void mixed_load_tile_pairs(float4* sA, float4* sB, float2* sC,
+                                                      const float4* __restrict__ jA,
+                                                      const float4* __restrict__ jB,
+                                                      const float2* __restrict__ jC, int64_t j0, int64_t jhi) {
+  const PairTile<JT> t(sA, sB, sC);
+#pragma unroll
+  for (int q = threadIdx.x; q < JT; q += NT) {
+    const int64_t j = min(j0 + q, jhi - 1);
+    const float* a = (const float*)&jA[j];
+    const float* b = (const float*)&jB[j];
+    const float* c = (const float*)&jC[j];
+    const int o = 4 * (q >> 1) + (q & 1);
+    cp_async4(t.p0 + o, a + 0);
+    cp_async4(t.p0 + o + 2, a + 1);
+    cp_async4(t.p1 + o, a + 2);
+    cp_async4(t.p1 + o + 2, a + 3);
+    cp_async4(t.p2 + o, b + 3);
+    cp_async4(t.p2 + o + 2, c + 0);
+    cp_async4(t.p3 + o, c + 1);
+    cp_async4(t.p3 + o + 2, b + 0);
+    cp_async4(t.p4 + o, b + 1);
+    cp_async4(t.p4 + o + 2, b + 2);
   }
 }
 
@@ -146,6 +196,64 @@ __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, c
       p[k][4] = fmaf(mr3, fmaf(a3, dy, wy), p[k][4]);
       p[k][5] = fmaf(mr3, fmaf(a3, dz, wz), p[k][5]);
     }
+  }
+}
+
+// The same pass for one i per thread on the pair layout: every FP32 operation
+// acts on the pair (j, j+1) at once (packed FP32x2 add/mul/fma, each lane
+// rounded exactly as its scalar counterpart), which halves the issue slots of
+// the FP32 work.  ni* hold the NEGATED i coordinates and velocity in both
+// lanes, so x_j + (-x_i) is the scalar x_j - x_i bit for bit.  The two lanes
+// of p sum the even and the odd j of the tile.
+template <int JT, int MODE>
+__device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const float2 (&nxh)[3],
+                                                const float2 (&nxl)[3], const float2 (&nv)[3], int rel,
+                                                float2 eps2, float2 (&p)[7]) {
+  const float4* __restrict__ P0 = (const float4*)t.p0;
+  const float4* __restrict__ P1 = (const float4*)t.p1;
+  const float4* __restrict__ P2 = (const float4*)t.p2;
+  const float4* __restrict__ P3 = (const float4*)t.p3;
+  const float4* __restrict__ P4 = (const float4*)t.p4;
+  const float2 m3 = make_float2(-3.0f, -3.0f);
+  NB_PRAGMA_UNROLL(NB_MIXED_UNROLL)
+  for (int u = 0; u < JT / 2; ++u) {
+    const float4 a = P0[u], b = P1[u], c = P2[u], d = P3[u];
+    float2 dx = __fadd2_rn(make_float2(a.x, a.y), nxh[0]);
+    float2 dy = __fadd2_rn(make_float2(a.z, a.w), nxh[1]);
+    float2 dz = __fadd2_rn(make_float2(b.x, b.y), nxh[2]);
+    if (MODE != kFar) {
+      const float4 e = P4[u];
+      dx = __fadd2_rn(dx, __fadd2_rn(make_float2(d.z, d.w), nxl[0]));
+      dy = __fadd2_rn(dy, __fadd2_rn(make_float2(e.x, e.y), nxl[1]));
+      dz = __fadd2_rn(dz, __fadd2_rn(make_float2(e.z, e.w), nxl[2]));
+    }
+    const float2 wx = __fadd2_rn(make_float2(c.x, c.y), nv[0]);
+    const float2 wy = __fadd2_rn(make_float2(c.z, c.w), nv[1]);
+    const float2 wz = __fadd2_rn(make_float2(d.x, d.y), nv[2]);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+    const float2 rw = __ffma2_rn(dz, wz, __ffma2_rn(dy, wy, __fmul2_rn(dx, wx)));
+#if NB_MIXED_NEWTON
+    const float2 y0 = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
+    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), __fmul2_rn(y0, y0), make_float2(1.0f, 1.0f));
+    float2 rinv = __ffma2_rn(make_float2(0.5f, 0.5f), __fmul2_rn(y0, e), y0);
+#else
+    float2 rinv = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
+#endif
+    if (MODE == kSelf) {
+      rinv.x = (2 * u == rel) ? 0.0f : rinv.x;
+      rinv.y = (2 * u + 1 == rel) ? 0.0f : rinv.y;
+    }
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 mr = __fmul2_rn(make_float2(b.z, b.w), rinv);
+    const float2 mr3 = __fmul2_rn(mr, rinv2);
+    const float2 a3 = __fmul2_rn(__fmul2_rn(rw, m3), rinv2);
+    p[6] = __fadd2_rn(p[6], mr);
+    p[0] = __ffma2_rn(mr3, dx, p[0]);
+    p[1] = __ffma2_rn(mr3, dy, p[1]);
+    p[2] = __ffma2_rn(mr3, dz, p[2]);
+    p[3] = __ffma2_rn(mr3, __ffma2_rn(a3, dx, wx), p[3]);
+    p[4] = __ffma2_rn(mr3, __ffma2_rn(a3, dy, wy), p[4]);
+    p[5] = __ffma2_rn(mr3, __ffma2_rn(a3, dz, wz), p[5]);
   }
 }
 
@@ -241,21 +349,51 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     }
   }
 
+  // packed loop: the i-particle in both lanes, negated
+  constexpr bool kPk = NB_MIXED_PACKED && IPT == 1;
+  float2 nxh[3], nxl[3], nv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    nxh[c] = make_float2(-xh[0][c], -xh[0][c]);
+    nxl[c] = make_float2(-xl[0][c], -xl[0][c]);
+    nv[c] = make_float2(-vi[0][c], -vi[0][c]);
+  }
+
   const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
-  if (ntiles > 0) mixed_load_tile<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
+  if (ntiles > 0) {
+    if constexpr (kPk)
+      mixed_load_tile_pairs<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
+    else
+      mixed_load_tile<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
+  }
   cp_async_commit();
 
   for (int tile = 0; tile < ntiles; ++tile) {
     const int buf = tile & 1;
     const int64_t jt = jlo + (int64_t)tile * JT;
-    if (tile + 1 < ntiles)
-      mixed_load_tile<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
+    if (tile + 1 < ntiles) {
+      if constexpr (kPk)
+        mixed_load_tile_pairs<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
+      else
+        mixed_load_tile<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     if (jt + JT > jhi) {  // ragged last tile: massless far-away particles past jhi
-      for (int q = tid; q < JT; q += NT)
-        if (jt + q >= jhi) sm.A[buf][q] = make_float4(kFarF, kFarF, kFarF, 0.0f);
+      for (int q = tid; q < JT; q += NT) {
+        if (jt + q < jhi) continue;
+        if constexpr (kPk) {
+          const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
+          const int o = 4 * (q >> 1) + (q & 1);
+          pt.p0[o] = kFarF;
+          pt.p0[o + 2] = kFarF;
+          pt.p1[o] = kFarF;
+          pt.p1[o + 2] = 0.0f;
+        } else {
+          sm.A[buf][q] = make_float4(kFarF, kFarF, kFarF, 0.0f);
+        }
+      }
       __syncthreads();
     }
 
@@ -285,12 +423,28 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
       const float lim = kFarTheta * (wr + blo.w);
       far = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
     }
-    if (__any_sync(0xffffffffu, hit))
-      mixed_tile_pass<IPT, JT, kSelf>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
-    else if (__all_sync(0xffffffffu, far))
-      mixed_tile_pass<IPT, JT, kFar>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
-    else
-      mixed_tile_pass<IPT, JT, kNear>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+    if constexpr (kPk) {
+      const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
+      const float2 e2 = make_float2(eps2, eps2);
+      float2 p2[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) p2[c] = make_float2(0.0f, 0.0f);
+      if (__any_sync(0xffffffffu, hit))
+        mixed_pair_pass<JT, kSelf>(pt, nxh, nxl, nv, rel[0], e2, p2);
+      else if (__all_sync(0xffffffffu, far))
+        mixed_pair_pass<JT, kFar>(pt, nxh, nxl, nv, rel[0], e2, p2);
+      else
+        mixed_pair_pass<JT, kNear>(pt, nxh, nxl, nv, rel[0], e2, p2);
+#pragma unroll
+      for (int c = 0; c < 7; ++c) p[0][c] = p2[c].x + p2[c].y;
+    } else {
+      if (__any_sync(0xffffffffu, hit))
+        mixed_tile_pass<IPT, JT, kSelf>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+      else if (__all_sync(0xffffffffu, far))
+        mixed_tile_pass<IPT, JT, kFar>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+      else
+        mixed_tile_pass<IPT, JT, kNear>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
+    }
 
 #pragma unroll
     for (int k = 0; k < IPT; ++k)

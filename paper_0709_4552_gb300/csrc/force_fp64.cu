@@ -85,8 +85,8 @@ bool nb_tuning_supported(int precision, const nb_tuning& cfg) {
 
 nb_tuning nb_default_tuning(int precision) {
   if (precision == NB_FP64) return nb_tuning{1, 128, 64, 0};
-  // one i per thread: 56 registers, 9 CTAs (36 warps) per SM; measured fastest
-  // at N = 2^20 (more i per thread saves shared loads but costs occupancy)
+  // one i per thread, two j per packed FP32x2 instruction: measured fastest at
+  // N = 2^20 (more i per thread saves shared loads but costs occupancy)
   return nb_tuning{1, 128, 128, 0};
 }
 

@@ -190,3 +190,20 @@ def test_autotune_picks_a_supported_launch(nbl):
             s.predict(0.0)
             got = s.compute_forces(idx.astype(np.int32))
         _check(P, nbl, got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_degenerate_sizes(nbl, prec):
+    # one particle: no pair, zero force and potential; empty active list: no-op
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    with nbl.NBody(4, P, 0) as s:
+        s.set_params(0.01, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, np.array([1.0]), np.array([[0.1, 0.2, 0.3]]), np.array([[1.0, 0.0, 0.0]]))
+        s.predict(0.0)
+        a, j, p = s.compute_forces(np.array([0], dtype=np.int32))
+        assert np.all(a == 0.0) and np.all(j == 0.0) and np.all(p == 0.0)
+        a, j, p = s.compute_forces(np.zeros(0, dtype=np.int32))
+        assert a.shape == (0, 3)
+        s.initial_forces_and_dt()
+        t, n = s.step()
+        assert n == 1 and t == 2.0 ** -3
