@@ -234,7 +234,7 @@ int nb_set_tuning(nb_ctx* ctx, int i_per_thread, int threads, int j_tile, int n_
  * nb_autotune -- time the supported force launches for the current N and
  * active-block size n on the current state (needs a prediction) and keep the
  * fastest for blocks of about that size.  Writes the chosen configuration
- * (any pointer may be NULL).
+ * (any pointer may be NULL; *n_split = 0 means the automatic split).
  */
 int nb_autotune(nb_ctx* ctx, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split);
 

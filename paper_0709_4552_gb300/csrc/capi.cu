@@ -62,7 +62,7 @@ void free_ctx(nb_ctx* c) {
   void* dptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->jA, c->jB,
                    c->jC, c->F, c->part, c->act, c->ident, c->ulist, c->sel_min, c->sel_cnt, c->red,
                    c->status, c->d_offsets, c->d_ceps, c->perm, c->iperm, c->skey[0], c->skey[1],
-                   c->sval[0], c->sval[1], c->shist, c->tbox};
+                   c->sval[0], c->sval[1], c->shist, c->tbox, c->mlist, c->pscratch};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -164,15 +164,46 @@ int get_scalar(nb_ctx* c, const double* src, double* dst, int64_t count, int ptr
   return NB_OK;
 }
 
+// particles [first, first + count) of a state array of `rows` rows to the
+// caller (AoS for 3 rows); gathered through iperm in the resident order.
+// Host copies are complete on return.
+int get_rows(nb_ctx* c, const double* src, int rows, int64_t first, int64_t count, double* dst, int ptr_kind) {
+  if (!dst) return NB_OK;
+  int r;
+  if (!c->perm_valid) {
+    r = rows == 3 ? get_vec(c, src + first, c->n_pad, dst, count, ptr_kind)
+                  : get_scalar(c, src + first, dst, count, ptr_kind);
+  } else {
+    NB_CUDA(c, nb_gather_rows(c, src, rows, first, count, ptr_kind == NB_PTR_HOST ? c->part : dst));
+    r = NB_OK;
+    if (ptr_kind == NB_PTR_HOST)
+      NB_CUDA(c, cudaMemcpyAsync(dst, c->part, rows * count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (r) return r;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
 // (re)compute the spatial order of the j-store when the particles changed or
 // after sort_interval block steps; the next prediction writes that order
+// (mixed path only: the FP64 path has no far-tile pass to gain from it)
 int ensure_sorted(nb_ctx* c) {
-  if (c->n_clusters > 0 || c->n <= 0) return NB_OK;
+  if (c->n_clusters > 0 || c->n <= 0 || c->precision != NB_MIXED) return NB_OK;
   if (c->perm_valid && c->perm_age < c->sort_interval) return NB_OK;
   NB_CUDA(c, nb_spatial_sort(c));
   c->perm_valid = true;
   c->perm_age = 0;
   c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}
+
+// a caller's list on the device, as slots of the resident order
+int caller_list(nb_ctx* c, const int32_t* list, int64_t n, int ptr_kind, const int32_t** d_slots) {
+  const int32_t* d_list = nullptr;
+  int r = stage_list(c, list, n, ptr_kind, &d_list);
+  if (r) return r;
+  NB_CUDA(c, nb_map_to_slots(c, d_list, n, d_slots));
   return NB_OK;
 }
 
@@ -249,17 +280,14 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
   const nb_tuning cfg = pick_tuning(c, n);
   if (c->precision == NB_FP64) return nb_forces_fp64(c, d_list, n, cfg);
-  // mixed path with a spatial order: visit the list in that order.  The
-  // block-selection list already is; the identity list is visited as perm;
-  // any other list is sorted by the slots of its particles.
+  // mixed path in the resident spatial order: the block-selection list and
+  // the identity list are ascending slots, i.e. already in that order; a
+  // caller's list (mapped to slots) is visited sorted by slot.
   const int32_t* ord = nullptr;
-  if (c->perm_valid && c->n_clusters == 0 && d_list != c->act) {
-    if (d_list == c->ident && n == c->n) {
-      ord = c->perm;
-    } else if (n >= 8192 && n * 16 >= c->n) {  // sparse lists give loose warps anyway
-      cudaError_t e = nb_list_order(c, d_list, n, &ord);
-      if (e != cudaSuccess) return e;
-    }
+  if (c->perm_valid && c->n_clusters == 0 && d_list != c->act && d_list != c->ident &&
+      n >= 2048) {  // below that the sort costs more than the far tiles it finds
+    cudaError_t e = nb_list_order(c, d_list, n, &ord);
+    if (e != cudaSuccess) return e;
   }
   return nb_forces_mixed(c, d_list, n, cfg, ord);
 }
@@ -327,7 +355,7 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
   NB_ALLOC(c->jk, 3 * np) NB_ALLOC(c->pot, np) NB_ALLOC(c->t, np) NB_ALLOC(c->dt, np)
   NB_ALLOC(c->xp, 3 * np) NB_ALLOC(c->vp, 3 * np) NB_ALLOC(c->jA, np) NB_ALLOC(c->jB, np)
   NB_ALLOC(c->jC, np) NB_ALLOC(c->F, 7 * np) NB_ALLOC(c->part, (size_t)c->part_elems)
-  NB_ALLOC(c->act, np) NB_ALLOC(c->ident, np) NB_ALLOC(c->ulist, np)
+  NB_ALLOC(c->act, np) NB_ALLOC(c->ident, np) NB_ALLOC(c->ulist, np) NB_ALLOC(c->mlist, np)
   NB_ALLOC(c->sel_min, (size_t)c->sel_ctas + 1) NB_ALLOC(c->sel_cnt, (size_t)c->sel_ctas + 1)
   NB_ALLOC(c->red, NB_RED_DOUBLES) NB_ALLOC(c->status, 1)
   NB_ALLOC(c->perm, np) NB_ALLOC(c->iperm, np) NB_ALLOC(c->skey[0], np) NB_ALLOC(c->skey[1], np)
@@ -392,6 +420,7 @@ int nb_set_j_particles(nb_ctx* c, int64_t first, int64_t count, const double* m,
       (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
     return fail(c, NB_EINVAL);
   if (count == 0) return NB_OK;
+  NB_CUDA(c, nb_unsort(c));  // particle order while particles are written
   if (ptr_kind == NB_PTR_HOST) {
     const double* arrs[] = {m, x, v, a, jerk, t, dt};
     const int64_t lens[] = {count, 3 * count, 3 * count, 3 * count, 3 * count, count, count};
@@ -420,6 +449,8 @@ int nb_set_j_particles(nb_ctx* c, int64_t first, int64_t count, const double* m,
 int nb_set_n(nb_ctx* c, int64_t n) {
   if (!c) return NB_EINVAL;
   if (n < 0 || n > c->n_max) return fail(c, NB_EINVAL);
+  if (select_device(c) != NB_OK) return fail(c, NB_ECUDA);
+  NB_CUDA(c, nb_unsort(c));
   c->n = n;
   c->pred_valid = false;
   c->f_valid = false;
@@ -441,19 +472,11 @@ int nb_get_particles(nb_ctx* c, int64_t first, int64_t count, double* m, double*
     return fail(c, NB_EINVAL);
   if (count == 0) return NB_OK;
   int r;
-  // vectors pass through the staging area one at a time on the stream
-  const double* soa[] = {c->x, c->v, c->a, c->jk};
-  double* dst[] = {x, v, a, jerk};
-  for (int q = 0; q < 4; ++q) {
-    if (!dst[q]) continue;
-    if ((r = get_vec(c, soa[q] + first, c->n_pad, dst[q], count, ptr_kind))) return r;
-    if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
-  }
-  if ((r = get_scalar(c, c->m + first, m, count, ptr_kind))) return r;
-  if ((r = get_scalar(c, c->pot + first, pot, count, ptr_kind))) return r;
-  if ((r = get_scalar(c, c->t + first, t, count, ptr_kind))) return r;
-  if ((r = get_scalar(c, c->dt + first, dt, count, ptr_kind))) return r;
-  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  // one array at a time through the staging area
+  const double* src[] = {c->x, c->v, c->a, c->jk, c->m, c->pot, c->t, c->dt};
+  double* dst[] = {x, v, a, jerk, m, pot, t, dt};
+  for (int q = 0; q < 8; ++q)
+    if ((r = get_rows(c, src[q], q < 4 ? 3 : 1, first, count, dst[q], ptr_kind))) return r;
   return NB_OK;
 }
 
@@ -464,10 +487,12 @@ int nb_next_block(nb_ctx* c, double* t_next, int32_t* active_idx, int64_t* n_act
   int r = select_block(c, t_next, n_active);
   if (r) return r;
   if (active_idx && *n_active > 0) {
-    NB_CUDA(c, cudaMemcpyAsync(active_idx, c->act, *n_active * sizeof(int32_t), cudaMemcpyDeviceToHost,
+    // the device list holds slots of the resident order; the caller gets
+    // ascending particle indices
+    NB_CUDA(c, nb_map_to_particles(c, c->act, *n_active, c->ulist));
+    NB_CUDA(c, cudaMemcpyAsync(active_idx, c->ulist, *n_active * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
-    // the device list is in the j-store's spatial order; the caller gets ascending indices
     std::sort(active_idx, active_idx + *n_active);
   }
   return NB_OK;
@@ -493,7 +518,7 @@ int nb_compute_forces(nb_ctx* c, const int32_t* i_idx, int64_t n, double* acc, d
   if (n == 0) return NB_OK;
   if (!c->pred_valid) return fail(c, NB_ESTATE);
   const int32_t* d_list = nullptr;
-  int r = stage_list(c, i_idx, n, ptr_kind, &d_list);
+  int r = caller_list(c, i_idx, n, ptr_kind, &d_list);
   if (r) return r;
   NB_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
   NB_CUDA(c, nb_forces(c, d_list, n));
@@ -522,7 +547,7 @@ int nb_correct(nb_ctx* c, const int32_t* i_idx, int64_t n, double t, int ptr_kin
   if (n == 0) return NB_OK;
   if (!c->f_valid || c->f_n != n || !c->pred_valid) return fail(c, NB_ESTATE);
   const int32_t* d_list = nullptr;
-  int r = stage_list(c, i_idx, n, ptr_kind, &d_list);
+  int r = caller_list(c, i_idx, n, ptr_kind, &d_list);
   if (r) return r;
   NB_CUDA(c, nb_launch_correct(c, d_list, n, t));
   c->f_valid = false;
@@ -683,10 +708,12 @@ int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_ti
         nb_tuning cfg{c->precision == NB_MIXED ? ipt_mixed[ii] : 1, thr_list[ti],
                       c->precision == NB_MIXED ? jt_mixed[ji] : jt_fp64[ji], 0};
         if (!nb_tuning_supported(c->precision, cfg)) continue;
-        cfg.nsplit = nb_auto_split(c, n, cfg);
-        const int splits[] = {cfg.nsplit, std::max(1, cfg.nsplit / 2), cfg.nsplit * 2};
+        // the automatic split (0, sized from the kernel's occupancy) and a
+        // smaller and a larger explicit one
+        const int guess = nb_auto_split(c, n, cfg, 4);
+        const int splits[] = {0, std::max(1, guess / 2), guess * 2};
         for (int si = 0; si < 3; ++si) {
-          if (si > 0 && splits[si] == cfg.nsplit) continue;
+          if (si > 0 && (guess == 1 || splits[si] == splits[si - 1])) continue;
           nb_tuning t = cfg;
           t.nsplit = splits[si];
           c->tune_override = t;

@@ -413,23 +413,41 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
 }
 
 // split-j reduction per cluster, fixed order over splits
+// split-j reduction per slot of the active clusters: block = 32 slots x
+// kRedLanes split lanes for one row r (grid.y); lane y sums splits y,
+// y + kRedLanes, ... in order and a fixed binary tree combines the lanes
+// (one summation order per split count)
+constexpr int kRedLanes = 8;
 __global__ void b_reduce(int64_t N, const int32_t* __restrict__ cid, const int64_t* __restrict__ off,
                          const int32_t* __restrict__ nact, const int32_t* __restrict__ nsplit,
                          const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride,
                          const double* __restrict__ part, double* __restrict__ F, int64_t fstride) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-    const int c = cid[s];
-    const int64_t k = s - off[c];
-    const int S = nsplit[c];
-    if (k >= nact[c] || S <= 1) continue;
-    const double* p = part + part_off[c];
-    const int64_t ps = pstride[c];
-#pragma unroll
-    for (int r = 0; r < 7; ++r) {
-      double acc = 0.0;
-      for (int q = 0; q < S; ++q) acc += p[((int64_t)q * 7 + r) * ps + k];
-      F[r * fstride + s] = r == 6 ? -acc : acc;
+  __shared__ double sm[kRedLanes][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, r = blockIdx.y;
+  for (int64_t s0 = (int64_t)blockIdx.x * 32; s0 < N; s0 += (int64_t)gridDim.x * 32) {
+    const int64_t s = s0 + tx;
+    bool live = false;
+    double acc = 0.0;
+    if (s < N) {
+      const int c = cid[s];
+      const int64_t k = s - off[c];
+      const int S = nsplit[c];
+      live = k < nact[c] && S > 1;
+      if (live) {
+        const double* p = part + part_off[c];
+        const int64_t ps = pstride[c];
+        for (int q = ty; q < S; q += kRedLanes) acc += p[((int64_t)q * 7 + r) * ps + k];
+      }
     }
+    sm[ty][tx] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int h = kRedLanes / 2; h > 0; h >>= 1) {
+      if (ty < h) sm[ty][tx] += sm[ty + h][tx];
+      __syncthreads();
+    }
+    if (ty == 0 && live) F[r * fstride + s] = r == 6 ? -sm[0][tx] : sm[0][tx];
+    __syncthreads();
   }
 }
 
@@ -702,8 +720,8 @@ cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
     b_force_fp64<kF64NT, kF64JT><<<b->grid_fp64, kF64NT, 0, c->stream>>>(
         b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
         b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
-  b_reduce<<<g, 256, 0, c->stream>>>(b->N, b->cid, b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part,
-                                     c->F, c->n_pad);
+  b_reduce<<<dim3((unsigned)grid_for(b->N, 32, c->sm_count * 8), 7), dim3(32, kRedLanes), 0, c->stream>>>(
+      b->N, b->cid, b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part, c->F, c->n_pad);
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -968,6 +986,7 @@ int nb_ensemble_integrate(nb_ctx* c, double t_end, int mode) {
     int r = nb_set_params(ch, c->h_ceps[q], c->eta, c->dt_min, c->dt_max);
     if (r == NB_OK) r = nb_integrate(ch, t_end, 0);
     if (r != NB_OK) return r;
+    if (nb_unsort(ch) != cudaSuccess) return NB_ECUDA;  // back to particle order
     if (copy_state(c, o, ch, 0, n, c->stream) != cudaSuccess) return NB_ECUDA;
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NB_ECUDA;

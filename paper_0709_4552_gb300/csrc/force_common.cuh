@@ -67,6 +67,10 @@ namespace nbk {
 
 constexpr float kFarF = 1.0e15f;
 
+// first j-tile of split s when `tiles` tiles are shared by S splits as evenly
+// as possible (split sizes differ by at most one tile)
+__device__ __forceinline__ int64_t split_begin(int64_t s, int64_t S, int64_t tiles) { return s * tiles / S; }
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
@@ -266,14 +270,13 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
                                            int64_t jlo, int64_t jhi, int64_t idx_hi,
                                            const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                            float eps2, double* __restrict__ out, int64_t ostride,
-                                           bool finalize, const int32_t* __restrict__ iperm = nullptr,
-                                           const float4* __restrict__ tbox = nullptr,
+                                           bool finalize, const float4* __restrict__ tbox = nullptr,
                                            const int32_t* __restrict__ ord = nullptr) {
-  // ord (optional): the list positions in processing order (a caller's list
-  // visited in spatial order); results always go to the list positions.
-  // iperm (optional): j-store slot of each particle (spatial order); tbox
-  // (optional, JT == NB_BOX_TILE, tiles aligned to slot 0): per-tile boxes
-  // that allow the far-tile pass.
+  // list: j-store slots of the i-particles.  ord (optional): the list
+  // positions in processing order (a caller's list visited in spatial
+  // order); results always go to the list positions.  tbox (optional,
+  // JT == NB_BOX_TILE, tiles aligned to slot 0): per-tile boxes that allow
+  // the far-tile pass.
   const int tid = threadIdx.x;
   float xh[IPT][3], xl[IPT][3], vi[IPT][3];
   int64_t self[IPT];
@@ -312,10 +315,6 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     if (ord) pos = ord[pos];
     int64_t p = list[pos];
     p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
-    if (iperm) {
-      p = iperm[p];
-      p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);
-    }
     self[k] = p;  // j-store slot of this i
     const float4 A = jA[p], B = jB[p];
     const float2 C = jC[p];

@@ -2,6 +2,8 @@
 // (force_common.cuh; Sec. 4.1 step 4, Eq. 3), the accuracy reference path,
 // plus the split-j reduction shared with the mixed path and the automatic
 // split choice.
+#include <algorithm>
+
 #include "force_common.cuh"
 
 namespace {
@@ -9,12 +11,12 @@ namespace {
 template <int NT, int JT>
 __global__ void __launch_bounds__(NT) force_fp64_kernel(
     const double* __restrict__ xp, const double* __restrict__ vp, const double* __restrict__ m,
-    int64_t n_pad, int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t j_per_split,
+    int64_t n_pad, int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t tiles,
     double eps2, double* __restrict__ out, int64_t ostride, int finalize) {
   __shared__ nbk::Fp64Smem<JT> sm;
   const int split = blockIdx.y;
-  const int64_t jlo = (int64_t)split * j_per_split;
-  const int64_t jhi = min(jlo + j_per_split, n_j);
+  const int64_t jlo = nbk::split_begin(split, gridDim.y, tiles) * JT;
+  const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::fp64_item<NT, JT>(sm, xp, vp, m, n_pad, jlo, jhi, list, n, (int64_t)blockIdx.x * NT, eps2, o, ostride,
                          finalize != 0);
@@ -22,29 +24,46 @@ __global__ void __launch_bounds__(NT) force_fp64_kernel(
 
 // split-j reduction: F[c][k] = sum over s = 0..S-1 (in this order) of
 // part[s][c][k]; the potential is negated (kernels sum +m/s).
+// Split-j reduction of part[S][7][stride] into F (the sign of the potential
+// applied here).  Block = 32 list positions x QL split lanes for one row c:
+// lane y sums splits y, y + QL, y + 2 QL, ... in order, then a fixed binary
+// tree combines the lanes, so the result depends only on S and QL (one
+// launch configuration = one summation order), and a long split list is
+// read by QL warps at once instead of one dependent chain per position.
+template <int QL>
 __global__ void split_reduce_kernel(const double* __restrict__ part, int64_t stride, int nsplit,
                                     int64_t n, double* __restrict__ F, int64_t fstride) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  __shared__ double sm[QL][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.y;
+  for (int64_t k0 = (int64_t)blockIdx.x * 32; k0 < n; k0 += (int64_t)gridDim.x * 32) {
+    const int64_t k = k0 + tx;
+    double s = 0.0;
+    if (k < n)
+      for (int q = ty; q < nsplit; q += QL) s += part[((int64_t)q * 7 + c) * stride + k];
+    sm[ty][tx] = s;
+    __syncthreads();
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-      for (int q = 0; q < nsplit; ++q) s += part[((int64_t)q * 7 + c) * stride + k];
-      F[c * fstride + k] = c == 6 ? -s : s;
+    for (int h = QL / 2; h > 0; h >>= 1) {
+      if (ty < h) sm[ty][tx] += sm[ty + h][tx];
+      __syncthreads();
     }
+    if (ty == 0 && k < n) F[c * fstride + k] = c == 6 ? -sm[0][tx] : sm[0][tx];
+    __syncthreads();
   }
 }
 
 template <int NT, int JT>
-cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit) {
+cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg) {
+  static int per_sm = 0;  // resident CTAs per SM of this instantiation
+  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_fp64_kernel<NT, JT>, NT, 0) !=
+                         cudaSuccess)
+    return cudaGetLastError();
+  int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg, per_sm);
   const int64_t itiles = (n + NT - 1) / NT;
   const int64_t n_j = ((c->n + JT - 1) / JT) * JT;
   const int64_t tiles = n_j / JT;
   if (nsplit > tiles) nsplit = (int)tiles;
   if (nsplit < 1) nsplit = 1;
-  const int64_t tiles_per_split = (tiles + nsplit - 1) / nsplit;
-  nsplit = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
-  const int64_t j_per_split = tiles_per_split * JT;
   const bool fin = nsplit == 1;
   const int64_t ostride = fin ? c->n_pad : ((n + 31) / 32) * 32;
   double* out = fin ? c->F : c->part;
@@ -52,8 +71,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit) {
   dim3 grid((unsigned)itiles, (unsigned)nsplit);
   c->launches += fin ? 1 : 2;
   force_fp64_kernel<NT, JT><<<grid, NT, 0, c->stream>>>(c->xp, c->vp, c->m, c->n_pad, n_j, d_list, n,
-                                                        j_per_split, c->eps * c->eps, out, ostride,
-                                                        fin ? 1 : 0);
+                                                        tiles, c->eps * c->eps, out, ostride, fin ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
@@ -64,10 +82,14 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit) {
 cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit,
                                    int64_t stride) {
   (void)d_list;
-  int g = (int)((n + 255) / 256);
-  if (g > c->sm_count * 8) g = c->sm_count * 8;
+  int64_t g = (n + 31) / 32;
+  if (g > (int64_t)c->sm_count * 16) g = (int64_t)c->sm_count * 16;
   if (g < 1) g = 1;
-  split_reduce_kernel<<<g, 256, 0, c->stream>>>(c->part, stride, nsplit, n, c->F, c->n_pad);
+  const dim3 grid((unsigned)g, 7);
+  if (nsplit >= 32)
+    split_reduce_kernel<32><<<grid, dim3(32, 32), 0, c->stream>>>(c->part, stride, nsplit, n, c->F, c->n_pad);
+  else
+    split_reduce_kernel<4><<<grid, dim3(32, 4), 0, c->stream>>>(c->part, stride, nsplit, n, c->F, c->n_pad);
   return cudaGetLastError();
 }
 
@@ -90,30 +112,42 @@ nb_tuning nb_default_tuning(int precision) {
   return nb_tuning{1, 128, 128, 0};
 }
 
-// Split-j factor: enough CTAs for about four waves of resident CTAs on all
-// SMs, at least one j-tile per split, within the partial-sum scratch.
-int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg) {
+// Split-j factor: at least four waves of resident CTAs (per_sm per SM), the
+// count of CTAs chosen so that the last wave is nearly full and the splits'
+// tile counts nearly equal; at least one j-tile per split, within the
+// partial-sum scratch.
+int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg, int per_sm) {
   const int64_t per_cta = (int64_t)cfg.threads * cfg.ipt;
   const int64_t itiles = (n + per_cta - 1) / per_cta;
-  const int64_t resident = (int64_t)c->sm_count * (cfg.threads <= 128 ? 4 : 2);
-  const int64_t want = 4 * resident;
-  if (itiles >= want) return 1;
-  int64_t s = (want + itiles - 1) / itiles;
+  const int64_t R = (int64_t)c->sm_count * (per_sm > 0 ? per_sm : 1);
+  if (itiles >= 4 * R) return 1;
   const int64_t tiles = (c->n + cfg.jtile - 1) / cfg.jtile;
-  if (s > tiles) s = tiles;
   const int64_t ostride = ((n + 31) / 32) * 32;
-  const int64_t cap = c->part_elems / (7 * ostride);
-  if (s > cap) s = cap;
-  if (s > 4096) s = 4096;
-  return (int)(s < 1 ? 1 : s);
+  int64_t cap = std::min<int64_t>(tiles, c->part_elems / (7 * ostride));
+  cap = std::min<int64_t>(cap, 4096);
+  if (cap < 1) return 1;
+  const int64_t s0 = std::min<int64_t>((4 * R + itiles - 1) / itiles, cap);
+  int64_t best = s0;
+  double best_e = -1.0;
+  for (int64_t s = s0; s <= std::min<int64_t>(cap, 2 * s0); ++s) {
+    const int64_t total = itiles * s;
+    const int64_t waves = (total + R - 1) / R;
+    const int64_t tmax = (tiles + s - 1) / s;  // tiles of the longest split
+    const double e = ((double)total / (double)(waves * R)) * ((double)tiles / (double)(s * tmax));
+    if (e > best_e + 1e-9) {
+      best = s;
+      best_e = e;
+    }
+    if (e >= 0.95) break;
+  }
+  return (int)best;
 }
 
 #define NB_FP64_CASE(NT_, JT_) \
-  if (cfg.threads == NT_ && cfg.jtile == JT_) return launch<NT_, JT_>(c, d_list, n, nsplit);
+  if (cfg.threads == NT_ && cfg.jtile == JT_) return launch<NT_, JT_>(c, d_list, n, cfg);
 
 cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg) {
   if (n <= 0) return cudaSuccess;
-  const int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg);
   NB_FP64_CASE(64, 32) NB_FP64_CASE(64, 64) NB_FP64_CASE(64, 128)
   NB_FP64_CASE(128, 32) NB_FP64_CASE(128, 64) NB_FP64_CASE(128, 128)
   NB_FP64_CASE(256, 32) NB_FP64_CASE(256, 64) NB_FP64_CASE(256, 128)

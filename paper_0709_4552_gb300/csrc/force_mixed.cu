@@ -23,41 +23,42 @@ namespace {
 template <int NT, int IPT, int JT>
 __global__ void NB_MIXED_BOUNDS(NT, IPT) force_mixed_kernel(
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
-    int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t j_per_split, float eps2,
-    double* __restrict__ out, int64_t ostride, int finalize, const int32_t* __restrict__ iperm,
-    const float4* __restrict__ tbox, const int32_t* __restrict__ ord) {
+    int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t tiles, float eps2,
+    double* __restrict__ out, int64_t ostride, int finalize, const float4* __restrict__ tbox,
+    const int32_t* __restrict__ ord) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   const int split = blockIdx.y;
-  const int64_t jlo = (int64_t)split * j_per_split;
-  const int64_t jhi = min(jlo + j_per_split, n_j);
+  const int64_t jlo = nbk::split_begin(split, gridDim.y, tiles) * JT;
+  const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * (NT * IPT),
-                               eps2, o, ostride, finalize != 0, iperm, tbox, ord);
+                               eps2, o, ostride, finalize != 0, tbox, ord);
 }
 
 template <int NT, int IPT, int JT>
-cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit, float eps2, const int32_t* ord) {
+cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg, float eps2,
+                   const int32_t* ord) {
+  static int per_sm = 0;  // resident CTAs per SM of this instantiation
+  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_mixed_kernel<NT, IPT, JT>, NT,
+                                                                   0) != cudaSuccess)
+    return cudaGetLastError();
+  int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg, per_sm);
   const int64_t per_cta = (int64_t)NT * IPT;
   const int64_t itiles = (n + per_cta - 1) / per_cta;
   const int64_t n_j = ((c->n + JT - 1) / JT) * JT;  // padding particles (m = 0) fill the last tile
   const int64_t tiles = n_j / JT;
   if (nsplit > tiles) nsplit = (int)tiles;
   if (nsplit < 1) nsplit = 1;
-  const int64_t tiles_per_split = (tiles + nsplit - 1) / nsplit;
-  nsplit = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
-  const int64_t j_per_split = tiles_per_split * JT;
   dim3 grid((unsigned)itiles, (unsigned)nsplit);
   const bool fin = nsplit == 1;
   const int64_t ostride = fin ? c->n_pad : ((n + 31) / 32) * 32;
   double* out = fin ? c->F : c->part;
   if (!fin && (int64_t)nsplit * 7 * ostride > c->part_elems) return cudaErrorInvalidValue;
   c->launches += fin ? 1 : 2;
-  // spatial order: i slots through iperm; far-tile boxes when the tiles match
-  const int32_t* iperm = c->perm_valid ? c->iperm : nullptr;
+  // resident spatial order: far-tile boxes when the tiles match
   const float4* tbox = (c->perm_valid && JT == NB_BOX_TILE) ? c->tbox : nullptr;
-  force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n,
-                                                              j_per_split, eps2, out, ostride, fin ? 1 : 0,
-                                                              iperm, tbox, iperm ? ord : nullptr);
+  force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n, tiles,
+                                                              eps2, out, ostride, fin ? 1 : 0, tbox, ord);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
@@ -74,13 +75,12 @@ bool nb_mixed_supported(const nb_tuning& t) {
 
 #define NB_MIXED_CASE(NT_, IPT_, JT_)                            \
   if (cfg.threads == NT_ && cfg.ipt == IPT_ && cfg.jtile == JT_) \
-    return launch<NT_, IPT_, JT_>(c, d_list, n, nsplit, eps2, ord);
+    return launch<NT_, IPT_, JT_>(c, d_list, n, cfg, eps2, ord);
 
 cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
                             const int32_t* ord) {
   if (n <= 0) return cudaSuccess;
   const float eps2 = (float)(c->eps * c->eps);
-  const int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg);
 #define NB_MIXED_JT(NT_, IPT_) NB_MIXED_CASE(NT_, IPT_, 64) NB_MIXED_CASE(NT_, IPT_, 128) NB_MIXED_CASE(NT_, IPT_, 256)
 #define NB_MIXED_IPT(NT_) NB_MIXED_JT(NT_, 1) NB_MIXED_JT(NT_, 2) NB_MIXED_JT(NT_, 4)
   NB_MIXED_IPT(64)

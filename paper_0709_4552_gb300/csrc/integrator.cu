@@ -30,43 +30,40 @@ __global__ void predict_kernel(int64_t N, int64_t n_pad, const double* __restric
                                const double* __restrict__ ti, double t, int own_time,
                                double* __restrict__ xp, double* __restrict__ vp,
                                float4* __restrict__ jA, float4* __restrict__ jB,
-                               float2* __restrict__ jC, int write_fp64, int write_mixed,
-                               const int32_t* __restrict__ perm) {
-  // slot k of the mixed j-store holds particle perm[k] (spatial order) or k;
-  // the FP64 arrays stay in particle order
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_pad;
-       k += (int64_t)gridDim.x * blockDim.x) {
+                               float2* __restrict__ jC, int write_fp64, int write_mixed) {
+  // rows in the resident order: row i of every array is one particle
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
     double px[3], pv[3], mi;
-    const int64_t i = (perm && k < N) ? (int64_t)perm[k] : k;
     if (i < N) {
       const double h = own_time ? 0.0 : t - ti[i];
       mi = m[i];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int64_t q = k * n_pad + i;
+      for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * n_pad + i;
         const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
-        px[k] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
-        pv[k] = vv + h * (av + h * (0.5 * jv));
+        px[d] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
+        pv[d] = vv + h * (av + h * (0.5 * jv));
       }
     } else {
       mi = 0.0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { px[k] = NB_PAD_POS; pv[k] = 0.0; }
+      for (int d = 0; d < 3; ++d) { px[d] = NB_PAD_POS; pv[d] = 0.0; }
     }
     if (write_fp64) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { xp[k * n_pad + i] = px[k]; vp[k * n_pad + i] = pv[k]; }
+      for (int d = 0; d < 3; ++d) { xp[d * n_pad + i] = px[d]; vp[d * n_pad + i] = pv[d]; }
     }
     if (write_mixed) {
       float hi[3], lo[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        hi[k] = __double2float_rn(px[k]);
-        lo[k] = __double2float_rn(px[k] - (double)hi[k]);
+      for (int d = 0; d < 3; ++d) {
+        hi[d] = __double2float_rn(px[d]);
+        lo[d] = __double2float_rn(px[d] - (double)hi[d]);
       }
-      jA[k] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(mi));
-      jB[k] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
-      jC[k] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
+      jA[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(mi));
+      jB[i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
+      jC[i] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
     }
   }
 }
@@ -262,16 +259,12 @@ __global__ void sel_min_final_kernel(int nb, unsigned long long* __restrict__ mi
 __global__ void sel_count_kernel(int64_t N, int64_t chunk, const double* __restrict__ ti,
                                  const double* __restrict__ dt,
                                  const unsigned long long* __restrict__ tmin, int nb,
-                                 int32_t* __restrict__ cnt, const int32_t* __restrict__ perm) {
-  // slots k in spatial order (particle perm[k]) when a spatial order exists
+                                 int32_t* __restrict__ cnt) {
   const double tn = __longlong_as_double((long long)tmin[nb]);
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = min(lo + chunk, N);
   int c = 0;
-  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-    const int64_t i = perm ? perm[k] : k;
-    c += (ti[i] + dt[i] == tn) ? 1 : 0;
-  }
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += (ti[i] + dt[i] == tn) ? 1 : 0;
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   __shared__ int sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = c;
@@ -306,8 +299,7 @@ __global__ void sel_scan_kernel(int nb, int32_t* __restrict__ cnt) {
 __global__ void sel_write_kernel(int64_t N, int64_t chunk, const double* __restrict__ ti,
                                  const double* __restrict__ dt,
                                  const unsigned long long* __restrict__ tmin, int nb,
-                                 const int32_t* __restrict__ off, int32_t* __restrict__ act,
-                                 const int32_t* __restrict__ perm) {
+                                 const int32_t* __restrict__ off, int32_t* __restrict__ act) {
   const double tn = __longlong_as_double((long long)tmin[nb]);
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = min(lo + chunk, N);
@@ -315,9 +307,8 @@ __global__ void sel_write_kernel(int64_t N, int64_t chunk, const double* __restr
   int base = off[blockIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t seg = lo; seg < hi; seg += blockDim.x) {
-    const int64_t k = seg + threadIdx.x;
-    const int64_t i = (k < hi) ? (perm ? (int64_t)perm[k] : k) : 0;
-    const bool f = (k < hi) && (ti[i] + dt[i] == tn);
+    const int64_t i = seg + threadIdx.x;
+    const bool f = (i < hi) && (ti[i] + dt[i] == tn);
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     const int pre = __popc(bal & ((1u << lane) - 1u));
     if (lane == 0) wsum[wid] = __popc(bal);
@@ -425,7 +416,7 @@ cudaError_t nb_launch_predict(nb_ctx* c, double t, bool own_time) {
   c->launches += 1;
   predict_kernel<<<grid_for(c->n_pad, kThreads, c->sm_count * 16), kThreads, 0, c->stream>>>(
       c->n, c->n_pad, c->m, c->x, c->v, c->a, c->jk, c->t, t, own_time ? 1 : 0, c->xp, c->vp, c->jA,
-      c->jB, c->jC, 1, mixed ? 1 : 0, c->perm_valid ? c->perm : nullptr);
+      c->jB, c->jC, 1, mixed ? 1 : 0);
   if (mixed && c->perm_valid) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -449,8 +440,7 @@ cudaError_t nb_launch_select(nb_ctx* c) {
                         cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
   }
-  const int32_t* perm = c->perm_valid ? c->perm : nullptr;  // spatially ordered active list
-  sel_count_kernel<<<used, 256, 0, c->stream>>>(c->n, chunk, c->t, c->dt, c->sel_min, nb, c->sel_cnt, perm);
+  sel_count_kernel<<<used, 256, 0, c->stream>>>(c->n, chunk, c->t, c->dt, c->sel_min, nb, c->sel_cnt);
   sel_scan_kernel<<<1, 1024, 0, c->stream>>>(used, c->sel_cnt);
   if (used != nb) {
     e = cudaMemcpyAsync(c->sel_cnt + nb, c->sel_cnt + used, sizeof(int32_t), cudaMemcpyDeviceToDevice,
@@ -458,7 +448,7 @@ cudaError_t nb_launch_select(nb_ctx* c) {
     if (e != cudaSuccess) return e;
   }
   sel_write_kernel<<<used, 256, 0, c->stream>>>(c->n, chunk, c->t, c->dt, c->sel_min, nb, c->sel_cnt,
-                                               c->act, perm);
+                                               c->act);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,14 @@
 //     F[7][n_pad] = (ax, ay, az, jx, jy, jz, pot), FP64        56 B/particle
 //   split-j partial sums: part[n_split][7][n_i]                (bounded)
 //   active list: act[n_pad] (int32, ascending), identity list ident[n_pad]
+//
+// Resident order: in the mixed path every per-particle array above is stored
+// in the spatial (Morton) order of the particles once it has been computed
+// (perm_valid): row s holds particle perm[s].  Every kernel works on rows
+// ("slots"); particle indices exist only at the C ABI, which maps caller
+// lists through iperm and returns particles through perm.  The arrays keep
+// their addresses when the order changes (the permutation goes through a
+// scratch block and back), so captured CUDA graphs stay valid.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -86,13 +94,15 @@ struct nb_ctx {
   int32_t* sel_cnt;             // per-CTA counts [sel_ctas] + total at [sel_ctas]
   int sel_ctas;
   double* red;                  // reduction scratch [NB_RED_DOUBLES]
-  // spatial (Morton) order of the mixed j-store (spatial.cu)
+  // resident spatial (Morton) order of the particle arrays (spatial.cu)
   int32_t *perm, *iperm;        // perm[slot] = particle, iperm[particle] = slot
+  int32_t* mlist;               // a caller's list mapped to slots
+  double* pscratch;             // 16 x n_pad doubles for reordering (allocated on first use)
   uint32_t* skey[2];            // radix-sort key buffers
   int32_t* sval[2];             // radix-sort value buffers
   int32_t* shist;               // radix-sort digit histograms
   float4* tbox;                 // per j-tile box: (lo, rmax), (hi, 0)
-  bool perm_valid;              // perm describes the current particles
+  bool perm_valid;              // the arrays are in the order perm (else slot = particle)
   int perm_age;                 // block steps since the last sort
   int sort_interval;            // re-sort after this many block steps
   // device status
@@ -145,15 +155,23 @@ cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, 
                                    int64_t stride);
 bool nb_tuning_supported(int precision, const nb_tuning& cfg);
 nb_tuning nb_default_tuning(int precision);
-int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg);
+// split-j factor for a kernel with per_sm resident CTAs per SM
+int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg, int per_sm);
 
 // the force dispatcher (capi.cu): picks the tuning and precision path
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
 
 // spatial.cu
-cudaError_t nb_spatial_sort(nb_ctx* c);       // perm / iperm from the current positions
+cudaError_t nb_spatial_sort(nb_ctx* c);       // new resident order from the current positions
+cudaError_t nb_unsort(nb_ctx* c);             // back to particle order (perm_valid = false)
+// caller list of particles -> list of slots in c->mlist (*out = d_list when unsorted)
+cudaError_t nb_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out);
+// slots -> particles: out[k] = perm[in[k]] (in == out allowed)
+cudaError_t nb_map_to_particles(nb_ctx* c, const int32_t* in, int64_t n, int32_t* out);
+// rows of particles [first, first + count) of a state array (rows x n_pad) to AoS dst
+cudaError_t nb_gather_rows(nb_ctx* c, const double* src, int rows, int64_t first, int64_t count, double* dst);
 cudaError_t nb_launch_tile_boxes(nb_ctx* c);  // tbox from the predicted (permuted) j-store
-// processing order of a caller's list in the spatial order (device array of n positions)
+// processing order of a list of slots: positions sorted by slot (device array of n positions)
 cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord);
 
 // ensemble.cu

@@ -1,18 +1,21 @@
-// spatial.cu -- spatial (Morton) order of the mixed path's j-store.
+// spatial.cu -- resident spatial (Morton) order of the mixed path.
 //
 // The mixed force kernel forms position differences from double-single pairs
 // (9 FP32 adds per pair).  When a warp's i-particles and a j-tile are far apart
 // compared with their distance from the origin, the FP32 "hi" parts alone give
 // the difference to FP32 accuracy (1 add per coordinate).  That needs warps
-// and tiles that are spatially compact, so the predictor writes the j-store
-// in Morton order of the particles' positions (perm[slot] = particle) and the
-// block selection lists active particles in the same order.  The order is a
-// pure layout choice: every sum is over the same pairs.
+// and tiles that are spatially compact, so the particle arrays are kept in
+// Morton order of the positions (row s holds particle perm[s]): the predictor,
+// block selection, force and corrector kernels then walk rows and every
+// access is coalesced, while the j-store and the active lists come out
+// spatially ordered.  The order is a pure layout choice: every sum is over
+// the same pairs.
 //
 // nb_spatial_sort: bounding box -> 30-bit Morton keys on a 1024^3 grid ->
 // stable least-significant-digit radix sort (4 passes of 8 bits; per-block
-// digit histograms, one scan, stable scatter ranked with warp match) ->
-// perm and its inverse.  Deterministic.
+// digit histograms, one scan, stable scatter ranked with warp match) -> the
+// rows gathered into a scratch block and copied back, perm composed and
+// inverted.  Deterministic.
 // nb_launch_tile_boxes: per j-tile of 128 slots, the box of the FP32 hi
 // positions of its real particles and their largest |coordinate|.
 #include <float.h>
@@ -207,15 +210,90 @@ int grid_for(int64_t n, int threads, int cap) {
   return (int)g;
 }
 
-// keys: slot of each listed particle (clamped); values: list positions
-__global__ void list_keys(const int32_t* __restrict__ list, int64_t n, const int32_t* __restrict__ iperm,
-                          int64_t N, uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+// keys: the listed slots (clamped); values: list positions
+__global__ void list_keys(const int32_t* __restrict__ list, int64_t n, int64_t N, uint32_t* __restrict__ key,
+                          int32_t* __restrict__ val) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = list[k];
     p = p < 0 ? 0 : (p >= N ? N - 1 : p);
-    key[k] = (uint32_t)iperm[p];
+    key[k] = (uint32_t)p;
     val[k] = (int32_t)k;
   }
+}
+
+// the 16 FP64 rows of the master state: m, x[3], v[3], a[3], jerk[3], pot, t, dt
+constexpr int kStateRows = 16;
+struct StateRows {
+  double* row[kStateRows];
+};
+
+StateRows state_rows(nb_ctx* c) {
+  StateRows r;
+  double* arr[8] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt};
+  const int cnt[8] = {1, 3, 3, 3, 3, 1, 1, 1};
+  int q = 0;
+  for (int i = 0; i < 8; ++i)
+    for (int k = 0; k < cnt[i]; ++k) r.row[q++] = arr[i] + (int64_t)k * c->n_pad;
+  return r;
+}
+
+// scratch[q][s] = row_q[src[s]] for s < N (a gather of every state row)
+__global__ void gather_state(int64_t N, int64_t n_pad, StateRows rows, const int32_t* __restrict__ src,
+                             double* __restrict__ scratch) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t from = src[s];
+#pragma unroll
+    for (int q = 0; q < kStateRows; ++q) scratch[q * n_pad + s] = rows.row[q][from];
+  }
+}
+
+__global__ void copy_state_back(int64_t N, int64_t n_pad, StateRows rows, const double* __restrict__ scratch) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int q = 0; q < kStateRows; ++q) rows.row[q][s] = scratch[q * n_pad + s];
+}
+
+// out[s] = a[b[s]] (composition of two orders), or b[s] when a is null
+__global__ void compose(int64_t N, const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                        int32_t* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+    out[s] = a ? a[b[s]] : b[s];
+}
+
+// out[k] = map[in[k]] with in[k] clamped to [0, N) (in == out allowed)
+__global__ void map_list(const int32_t* in, int64_t n, const int32_t* __restrict__ map, int64_t N, int32_t* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = in[k];
+    p = p < 0 ? 0 : (p >= N ? N - 1 : p);
+    out[k] = map[p];
+  }
+}
+
+// dst[k * rows + r] = src[r * n_pad + iperm[first + k]]
+__global__ void gather_rows(const double* __restrict__ src, int rows, int64_t n_pad, const int32_t* __restrict__ iperm,
+                            int64_t first, int64_t count, double* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = iperm[first + k];
+    for (int r = 0; r < rows; ++r) dst[k * rows + r] = src[r * n_pad + s];
+  }
+}
+
+// reorder every state row by src (new row s = old row src[s]) in place
+cudaError_t reorder_state(nb_ctx* c, const int32_t* src) {
+  if (!c->pscratch) {
+    cudaError_t e = cudaMalloc(&c->pscratch, (size_t)kStateRows * c->n_pad * sizeof(double));
+    if (e != cudaSuccess) {
+      c->pscratch = nullptr;
+      return e;
+    }
+  }
+  const StateRows rows = state_rows(c);
+  const int g = grid_for(c->n, 256, c->sm_count * 16);
+  gather_state<<<g, 256, 0, c->stream>>>(c->n, c->n_pad, rows, src, c->pscratch);
+  copy_state_back<<<g, 256, 0, c->stream>>>(c->n, c->n_pad, rows, c->pscratch);
+  c->launches += 2;
+  return cudaGetLastError();
 }
 
 // stable LSD radix sort of (skey[0], sval[0])[0..n) on the low `bits` bits;
@@ -249,20 +327,67 @@ cudaError_t nb_spatial_sort(nb_ctx* c) {
   int cur = 0;
   cudaError_t e = sort_pairs(c, N, 30, &cur);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(c->perm, c->sval[cur], N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  // sval[cur][s] = the current row that becomes row s
+  const int32_t* sigma = c->sval[cur];
+  e = reorder_state(c, sigma);
   if (e != cudaSuccess) return e;
-  invert_perm<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->perm, c->iperm);
-  c->launches += 4;
+  const int g = grid_for(N, 256, c->sm_count * 16);
+  int32_t* np = c->sval[cur ^ 1];
+  compose<<<g, 256, 0, c->stream>>>(N, c->perm_valid ? c->perm : nullptr, sigma, np);
+  e = cudaMemcpyAsync(c->perm, np, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  invert_perm<<<g, 256, 0, c->stream>>>(N, c->perm, c->iperm);
+  c->launches += 5;
   return cudaGetLastError();
 }
 
-// Processing order of a caller's active list in the spatial order: list
-// positions sorted by the j-store slot of their particle (stable).  The
-// mixed kernel then forms warps of nearby particles; results still go to the
-// caller's positions.  Returns a device array of n positions.
+cudaError_t nb_unsort(nb_ctx* c) {
+  if (!c->perm_valid) return cudaSuccess;
+  // particle p = old row iperm[p]
+  cudaError_t e = reorder_state(c, c->iperm);
+  if (e != cudaSuccess) return e;
+  c->perm_valid = false;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return cudaSuccess;
+}
+
+cudaError_t nb_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out) {
+  if (!c->perm_valid || n <= 0) {
+    *out = d_list;
+    return cudaSuccess;
+  }
+  map_list<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(d_list, n, c->iperm, c->n, c->mlist);
+  c->launches += 1;
+  *out = c->mlist;
+  return cudaGetLastError();
+}
+
+cudaError_t nb_map_to_particles(nb_ctx* c, const int32_t* in, int64_t n, int32_t* out) {
+  if (n <= 0) return cudaSuccess;
+  if (!c->perm_valid) {
+    if (in == out) return cudaSuccess;
+    return cudaMemcpyAsync(out, in, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  }
+  map_list<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(in, n, c->perm, c->n, out);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t nb_gather_rows(nb_ctx* c, const double* src, int rows, int64_t first, int64_t count, double* dst) {
+  if (count <= 0) return cudaSuccess;
+  gather_rows<<<grid_for(count, 256, c->sm_count * 16), 256, 0, c->stream>>>(src, rows, c->n_pad, c->iperm, first,
+                                                                             count, dst);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+// Processing order of a caller's active list (mapped to slots) in the
+// spatial order: list positions sorted by slot (stable).  The mixed kernel
+// then forms warps of nearby particles; results still go to the caller's
+// positions.  Returns a device array of n positions.
 cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord) {
-  list_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(d_list, n, c->iperm, c->n, c->skey[0],
-                                                                       c->sval[0]);
+  list_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(d_list, n, c->n, c->skey[0], c->sval[0]);
   int bits = 1;
   while (bits < 31 && ((int64_t)1 << bits) < c->n) ++bits;
   int cur = 0;

@@ -185,7 +185,7 @@ def test_autotune_picks_a_supported_launch(nbl):
             s.set_j_particles(0, m, x, v)
             s.predict(0.0)
             cfg = s.autotune(n)
-            assert cfg["threads"] in (64, 128, 256) and cfg["n_split"] >= 1
+            assert cfg["threads"] in (64, 128, 256) and cfg["n_split"] >= 0  # 0 = automatic
             assert cfg["i_per_thread"] in ((1,) if P == nbl.NB_FP64 else (1, 2, 4))
             s.predict(0.0)
             got = s.compute_forces(idx.astype(np.int32))

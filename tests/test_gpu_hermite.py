@@ -58,10 +58,12 @@ def test_block_steps_match(nbl, steps):
     assert np.abs(st["v"] - r["v"]).max() < 1e-11
 
 
-def test_next_block_matches_definition(nbl):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_next_block_matches_definition(nbl, prec):
     N = 3000
     m, x, v = inputs.plummer(N, 203, "salpeter")
-    with _ctx(nbl, m, x, v, 1 / 512, 0.01, 2.0 ** -22, 2.0 ** -3) as s:
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    with _ctx(nbl, m, x, v, 1 / 512, 0.01, 2.0 ** -22, 2.0 ** -3, prec=P) as s:
         for _ in range(5):
             st = _state(s, N)
             t, n, idx = s.next_block()
@@ -237,3 +239,50 @@ def test_dt_underflow_counted(nbl):
         st = _state(s, 3)
     assert code == nbl.NB_OK and under >= 2
     assert st["dt"][0] == 2.0 ** -12 and st["dt"][1] == 2.0 ** -12
+
+
+def test_resident_order_round_trip(nbl):
+    # a mixed context keeps its arrays in the spatial order of the particles;
+    # every ABI call still speaks particle indices
+    N, eps = 5000, 1 / 256
+    m, x, v = inputs.plummer(N, 207, "salpeter")
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()  # computes the order and reorders the arrays
+        st = s.get_particles(0, N)
+        for k, ref in (("m", m), ("x", x), ("v", v), ("t", np.zeros(N))):
+            assert np.array_equal(st[k], ref), k
+        a_ref, j_ref, p_ref = oracle.forces(m, x, v, eps)
+        assert rel_vec(st["a"], a_ref).max() < 1e-5 and rel_scalar(st["pot"], p_ref).max() < 1e-6
+        sub = s.get_particles(1234, 100)
+        assert np.array_equal(sub["m"], m[1234:1334]) and np.array_equal(sub["x"], x[1234:1334])
+        # device outputs take the same gather
+        torch = pytest.importorskip("torch")
+        dx = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        s.get_particles(0, N, out=dict(x=dx))
+        torch.cuda.synchronize()
+        assert np.array_equal(dx.cpu().numpy(), x)
+        # forces on a caller's list come back in the caller's order
+        idx = inputs.sample_indices(N, 900, 5)
+        s.predict(0.0)
+        a, _, p = s.compute_forces(idx.astype(np.int32))
+        assert rel_vec(a, a_ref[idx]).max() < 1e-5 and rel_scalar(p, p_ref[idx]).max() < 1e-6
+        for _ in range(3):
+            s.step()
+        st = s.get_particles(0, N)
+        t, n, act = s.next_block()
+        due = st["t"] + st["dt"]
+        assert t == due.min() and np.array_equal(act, np.nonzero(due == t)[0].astype(np.int32))
+        # overwrite a range: the rest keeps its state, the range reads back as written
+        x2 = x[100:200] * 1.5
+        s.set_j_particles(100, m[100:200], x2, v[100:200])
+        st2 = s.get_particles(0, N)
+        assert np.array_equal(st2["x"][100:200], x2)
+        keep = np.r_[0:100, 200:N]
+        for k in ("x", "v", "a", "t", "dt"):
+            assert np.array_equal(st2[k][keep], st[k][keep]), k
+        s.initial_forces_and_dt()
+        s.set_n(N - 10)
+        st3 = s.get_particles(0, N - 10)
+        assert np.array_equal(st3["m"], m[: N - 10]) and np.array_equal(st3["x"][100:200], x2)
