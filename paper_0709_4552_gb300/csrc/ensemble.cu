@@ -27,8 +27,13 @@
 namespace {
 
 constexpr int kSelChunk = 2048;   // particles per selection chunk (chunks never straddle clusters)
-constexpr int kMixNT = 128, kMixIPT = 1, kMixJT = 128;   // batched mixed item shape
-constexpr int kF64NT = 128, kF64JT = 64;                 // batched FP64 item shape
+// batched item shapes (i-tile = threads per CTA; small clusters have small
+// active blocks, so a shorter i-tile leaves fewer idle lanes)
+#ifndef NB_ENS_NT
+#define NB_ENS_NT 128
+#endif
+constexpr int kMixNT = NB_ENS_NT, kMixIPT = 1, kMixJT = 128;  // batched mixed item shape
+constexpr int kF64NT = NB_ENS_NT, kF64JT = 64;                // batched FP64 item shape
 constexpr int64_t kMaxIters = 50000000;                  // hard cap on loop iterations
 
 struct BParams {

@@ -275,8 +275,8 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
   // list: j-store slots of the i-particles.  ord (optional): the list
   // positions in processing order (a caller's list visited in spatial
   // order); results always go to the list positions.  tbox (optional,
-  // JT == NB_BOX_TILE, tiles aligned to slot 0): per-tile boxes that allow
-  // the far-tile pass.
+  // j-ranges aligned to JT slots): boxes of every NB_BOX_TILE slots up to
+  // the padded end of the j-store, which allow the far-tile pass.
   const int tid = threadIdx.x;
   float xh[IPT][3], xl[IPT][3], vi[IPT][3];
   int64_t self[IPT];
@@ -411,16 +411,23 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
       for (int c = 0; c < 7; ++c) p[k][c] = 0.0f;
 
     // far test (warp-uniform): box gap >= theta (|x|max of warp + |x|max of
-    // tile) bounds the hi-only difference error by 2^-24 (1/theta + 1)
+    // tile) bounds the hi-only difference error by 2^-24 (1/theta + 1).
+    // Boxes cover NB_BOX_TILE slots: a longer tile needs all of its boxes
+    // far, a shorter one uses the box that contains it.
     bool far = false;
     if (tbox) {
-      const int64_t t = jt / JT;
-      const float4 blo = tbox[2 * t], bhi = tbox[2 * t + 1];
-      const float gx = fmaxf(0.0f, fmaxf(blo.x - whi[0], wlo[0] - bhi.x));
-      const float gy = fmaxf(0.0f, fmaxf(blo.y - whi[1], wlo[1] - bhi.y));
-      const float gz = fmaxf(0.0f, fmaxf(blo.z - whi[2], wlo[2] - bhi.z));
-      const float lim = kFarTheta * (wr + blo.w);
-      far = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
+      constexpr int kBoxes = JT >= NB_BOX_TILE ? JT / NB_BOX_TILE : 1;
+      far = true;
+#pragma unroll
+      for (int b = 0; b < kBoxes; ++b) {
+        const int64_t t = jt / NB_BOX_TILE + b;
+        const float4 blo = tbox[2 * t], bhi = tbox[2 * t + 1];
+        const float gx = fmaxf(0.0f, fmaxf(blo.x - whi[0], wlo[0] - bhi.x));
+        const float gy = fmaxf(0.0f, fmaxf(blo.y - whi[1], wlo[1] - bhi.y));
+        const float gz = fmaxf(0.0f, fmaxf(blo.z - whi[2], wlo[2] - bhi.z));
+        const float lim = kFarTheta * (wr + blo.w);
+        far = far && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
+      }
     }
     if constexpr (kPk) {
       const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);

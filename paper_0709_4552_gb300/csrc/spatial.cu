@@ -172,7 +172,8 @@ __global__ void invert_perm(int64_t N, const int32_t* __restrict__ perm, int32_t
     iperm[perm[k]] = (int32_t)k;
 }
 
-// box of tile t (slots [t*JT, t*JT+JT) intersected with [0, N)): (lo, rmax), (hi, 0)
+// box of tile t (slots [t*JT, t*JT+JT) intersected with [0, N)): (lo, rmax), (hi, 0);
+// an empty intersection gives lo = +FLT_MAX, hi = -FLT_MAX, rmax = 0
 template <int JT>
 __global__ void tile_boxes(int64_t N, int64_t ntiles, const float4* __restrict__ jA, float4* __restrict__ box) {
   const int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
@@ -399,7 +400,8 @@ cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int
 }
 
 cudaError_t nb_launch_tile_boxes(nb_ctx* c) {
-  const int64_t ntiles = (c->n + NB_BOX_TILE - 1) / NB_BOX_TILE;
+  // every tile up to n_pad (tiles of padding alone get an empty box: always far)
+  const int64_t ntiles = c->n > 0 ? c->n_pad / NB_BOX_TILE : 0;
   if (ntiles <= 0) return cudaSuccess;
   const int warps = 8;
   tile_boxes<NB_BOX_TILE><<<(unsigned)((ntiles + warps - 1) / warps), warps * 32, 0, c->stream>>>(c->n, ntiles, c->jA,
