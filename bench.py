@@ -459,6 +459,18 @@ def run_integration(args):
             c1 = s.get_counters()
             k1, w1 = s.energy()
             s.close()
+            # the same time unit with the whole block-step loop on the device (one CUDA graph)
+            g = nb.NBody(N, nb.NB_MIXED, 0)
+            g.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
+            g.set_j_particles(0, m, x, v)
+            g.initial_forces_and_dt()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.integrate(1.0, use_graph=True)
+            torch.cuda.synchronize()
+            wall_g = time.perf_counter() - t0
+            kg, wg = g.energy()
+            g.close()
             steps = c1["block_steps"] - c0["block_steps"]
             inter = tim["interactions"]
             psteps = inter / N
@@ -469,7 +481,8 @@ def run_integration(args):
                         "tau_pred_s": tp / (steps * N), "tau_force_s": tf / inter, "tau_corr_s": tc / psteps,
                         "model_T_s": tp + tf + tc, "share_force": tf / wall, "share_pred": tp / wall,
                         "share_corr": tc / wall, "share_host_and_select": 1 - (tp + tf + tc) / wall,
-                        "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)})
+                        "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0),
+                        "T_app_graph_s": wall_g, "energy_drift_graph": abs((kg + wg) - (k0 + w0)) / abs(k0 + w0)})
             print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": "mixed",
                           "grape_tau_force_s": 4.3e-10, "rows": out}), flush=True)

@@ -84,6 +84,10 @@ void nb_destroy(nb_ctx* ctx);
  */
 int nb_set_params(nb_ctx* ctx, double eps, double eta, double dt_min, double dt_max);
 
+/* nb_get_params -- the context's eps, eta, dt_min, dt_max (any pointer may be
+ * NULL; no GPU work).  Errors: NB_EINVAL (ctx NULL). */
+int nb_get_params(nb_ctx* ctx, double* eps, double* eta, double* dt_min, double* dt_max);
+
 /* nb_default_params -- the paper's defaults (no context needed, no GPU). */
 void nb_default_params(double* eps, double* eta, double* dt_min, double* dt_max);
 

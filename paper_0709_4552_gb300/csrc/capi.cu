@@ -404,6 +404,15 @@ int nb_set_params(nb_ctx* c, double eps, double eta, double dt_min, double dt_ma
   return NB_OK;
 }
 
+int nb_get_params(nb_ctx* c, double* eps, double* eta, double* dt_min, double* dt_max) {
+  if (!c) return NB_EINVAL;
+  if (eps) *eps = c->eps;
+  if (eta) *eta = c->eta;
+  if (dt_min) *dt_min = c->dt_min;
+  if (dt_max) *dt_max = c->dt_max;
+  return NB_OK;
+}
+
 int nb_set_precision(nb_ctx* c, int precision) {
   if (!c) return NB_EINVAL;
   if (precision != NB_FP64 && precision != NB_MIXED) return fail(c, NB_EINVAL);

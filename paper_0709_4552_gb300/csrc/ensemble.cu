@@ -27,13 +27,12 @@
 namespace {
 
 constexpr int kSelChunk = 2048;   // particles per selection chunk (chunks never straddle clusters)
-// batched item shapes (i-tile = threads per CTA; small clusters have small
-// active blocks, so a shorter i-tile leaves fewer idle lanes)
-#ifndef NB_ENS_NT
-#define NB_ENS_NT 128
-#endif
-constexpr int kMixNT = NB_ENS_NT, kMixIPT = 1, kMixJT = 128;  // batched mixed item shape
-constexpr int kF64NT = NB_ENS_NT, kF64JT = 64;                // batched FP64 item shape
+// batched item shapes: i-tile = threads per CTA, one i per thread.  An
+// ensemble of small clusters has small active blocks (n = 0.20 N^0.81 is 18
+// at N = 256 and 169 at N = 4096), so it takes 32-particle i-tiles that
+// leave few lanes idle; the single-system graph loop takes 128.
+constexpr int kMixIPT = 1, kMixJT = 128;  // batched mixed item: j-tile
+constexpr int kF64JT = 64;                // batched FP64 item: j-tile
 constexpr int64_t kMaxIters = 50000000;                  // hard cap on loop iterations
 
 struct BParams {
@@ -69,6 +68,7 @@ struct Batch {
   double* esum = nullptr;          // [2C] per-cluster energies
   // host
   std::vector<int64_t> h_off;
+  int nt = 128;                    // i-tile (threads per CTA) of the force items: 32 or 128
   int grid_mixed = 0, grid_fp64 = 0;
   cudaGraphExec_t exec = nullptr;
   int exec_precision = -1;
@@ -418,41 +418,40 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
 }
 
 // split-j reduction per cluster, fixed order over splits
-// split-j reduction per slot of the active clusters: block = 32 slots x
-// kRedLanes split lanes for one row r (grid.y); lane y sums splits y,
-// y + kRedLanes, ... in order and a fixed binary tree combines the lanes
-// (one summation order per split count)
+// split-j reduction of the active clusters: block (c, y) = cluster c,
+// positions y*32 + 32*gridDim.y*q; 32 positions x kRedLanes split lanes; lane
+// y sums splits y, y + kRedLanes, ... in order and a fixed binary tree
+// combines the lanes (one summation order per split count).  Clusters with
+// one split wrote their results directly and leave at once.
 constexpr int kRedLanes = 8;
-__global__ void b_reduce(int64_t N, const int32_t* __restrict__ cid, const int64_t* __restrict__ off,
-                         const int32_t* __restrict__ nact, const int32_t* __restrict__ nsplit,
-                         const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride,
-                         const double* __restrict__ part, double* __restrict__ F, int64_t fstride) {
+constexpr int kRedChunks = 16;  // blocks per cluster
+__global__ void b_reduce(const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
+                         const int32_t* __restrict__ nsplit, const int64_t* __restrict__ part_off,
+                         const int64_t* __restrict__ pstride, const double* __restrict__ part,
+                         double* __restrict__ F, int64_t fstride) {
   __shared__ double sm[kRedLanes][33];
-  const int tx = threadIdx.x, ty = threadIdx.y, r = blockIdx.y;
-  for (int64_t s0 = (int64_t)blockIdx.x * 32; s0 < N; s0 += (int64_t)gridDim.x * 32) {
-    const int64_t s = s0 + tx;
-    bool live = false;
-    double acc = 0.0;
-    if (s < N) {
-      const int c = cid[s];
-      const int64_t k = s - off[c];
-      const int S = nsplit[c];
-      live = k < nact[c] && S > 1;
-      if (live) {
-        const double* p = part + part_off[c];
-        const int64_t ps = pstride[c];
+  const int c = blockIdx.x;
+  const int S = nsplit[c];
+  if (S <= 1) return;  // uniform over the block
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t n = nact[c], o = off[c], ps = pstride[c];
+  const double* p = part + part_off[c];
+  for (int64_t k0 = (int64_t)blockIdx.y * 32; k0 < n; k0 += (int64_t)gridDim.y * 32) {
+    const int64_t k = k0 + tx;
+    for (int r = 0; r < 7; ++r) {
+      double acc = 0.0;
+      if (k < n)
         for (int q = ty; q < S; q += kRedLanes) acc += p[((int64_t)q * 7 + r) * ps + k];
-      }
-    }
-    sm[ty][tx] = acc;
-    __syncthreads();
+      sm[ty][tx] = acc;
+      __syncthreads();
 #pragma unroll
-    for (int h = kRedLanes / 2; h > 0; h >>= 1) {
-      if (ty < h) sm[ty][tx] += sm[ty + h][tx];
+      for (int h = kRedLanes / 2; h > 0; h >>= 1) {
+        if (ty < h) sm[ty][tx] += sm[ty + h][tx];
+        __syncthreads();
+      }
+      if (ty == 0 && k < n) F[r * fstride + o + k] = r == 6 ? -sm[0][tx] : sm[0][tx];
       __syncthreads();
     }
-    if (ty == 0 && live) F[r * fstride + s] = r == 6 ? -sm[0][tx] : sm[0][tx];
-    __syncthreads();
   }
 }
 
@@ -671,12 +670,15 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
     fill_cid<<<grid_for(b->N, 256, 4096), 256, 0, c->stream>>>(b->N, b->off, C, b->cid);
     e = cudaGetLastError();
   }
+  b->nt = C > 1 ? 32 : 128;
   int per_sm = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<kMixNT, kMixIPT, kMixJT>, kMixNT, 0);
+    e = b->nt == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<32, kMixIPT, kMixJT>, 32, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<128, kMixIPT, kMixJT>, 128, 0);
   b->grid_mixed = std::max(1, per_sm) * c->sm_count;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<kF64NT, kF64JT>, kF64NT, 0);
+    e = b->nt == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<32, kF64JT>, 32, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<128, kF64JT>, 128, 0);
   b->grid_fp64 = std::max(1, per_sm) * c->sm_count;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host vectors go out of scope
   if (e != cudaSuccess) {
@@ -703,7 +705,7 @@ cudaError_t set_params(nb_ctx* c, Batch* b, double t_end) {
 // plan for the current active lists (b->nact, act), without loop control
 cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const bool mixed = c->precision == NB_MIXED;
-  const int per_cta = mixed ? kMixNT * kMixIPT : kF64NT;
+  const int per_cta = b->nt * (mixed ? kMixIPT : 1);
   const int jt = mixed ? kMixJT : kF64JT;
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
@@ -712,21 +714,29 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   return cudaGetLastError();
 }
 
+template <int NT>
+void launch_force(nb_ctx* c, Batch* b, bool mixed) {
+  if (mixed)
+    b_force_mixed<NT, kMixIPT, kMixJT><<<b->grid_mixed, NT, 0, c->stream>>>(
+        b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+  else
+    b_force_fp64<NT, kF64JT><<<b->grid_fp64, NT, 0, c->stream>>>(
+        b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+}
+
 cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
   const bool mixed = c->precision == NB_MIXED;
   const int g = grid_for(b->N, 256, c->sm_count * 16);
   b_predict<<<g, 256, 0, c->stream>>>(b->N, c->n_pad, b->cid, b->nact, b->tnext, own_time ? 1 : 0, c->m, c->x,
                                       c->v, c->a, c->jk, c->t, c->xp, c->vp, c->jA, c->jB, c->jC, 1, mixed ? 1 : 0);
-  if (mixed)
-    b_force_mixed<kMixNT, kMixIPT, kMixJT><<<b->grid_mixed, kMixNT, 0, c->stream>>>(
-        b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+  if (b->nt == 32)
+    launch_force<32>(c, b, mixed);
   else
-    b_force_fp64<kF64NT, kF64JT><<<b->grid_fp64, kF64NT, 0, c->stream>>>(
-        b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
-  b_reduce<<<dim3((unsigned)grid_for(b->N, 32, c->sm_count * 8), 7), dim3(32, kRedLanes), 0, c->stream>>>(
-      b->N, b->cid, b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part, c->F, c->n_pad);
+    launch_force<128>(c, b, mixed);
+  b_reduce<<<dim3((unsigned)b->C, kRedChunks), dim3(32, kRedLanes), 0, c->stream>>>(
+      b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part, c->F, c->n_pad);
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -734,7 +744,7 @@ cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
 // one block step of every active cluster, all on the device
 cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle, int use_handle) {
   const bool mixed = c->precision == NB_MIXED;
-  const int per_cta = mixed ? kMixNT * kMixIPT : kF64NT;
+  const int per_cta = b->nt * (mixed ? kMixIPT : 1);
   const int jt = mixed ? kMixJT : kF64JT;
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_sel_min<<<b->nchunks, 256, 0, c->stream>>>(b->ch_lo, b->ch_hi, c->t, c->dt, b->ch_min);

@@ -25,7 +25,7 @@ NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
 
 # every symbol include/nbody.h declares
 EXPORTS = (
-    "nb_create", "nb_destroy", "nb_set_params", "nb_default_params", "nb_set_precision",
+    "nb_create", "nb_destroy", "nb_set_params", "nb_get_params", "nb_default_params", "nb_set_precision",
     "nb_set_j_particles", "nb_set_n", "nb_get_n", "nb_get_particles", "nb_next_block", "nb_predict",
     "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_last_error", "nb_clear_error",
@@ -64,6 +64,7 @@ def lib():
         "nb_create": (_int, [ctypes.POINTER(_vp), _i64, _int, _int, _vp]),
         "nb_destroy": (None, [_vp]),
         "nb_set_params": (_int, [_vp, _d, _d, _d, _d]),
+        "nb_get_params": (_int, [_vp, _vp, _vp, _vp, _vp]),
         "nb_default_params": (None, [_pd, _pd, _pd, _pd]),
         "nb_set_precision": (_int, [_vp, _int]),
         "nb_set_j_particles": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int]),
@@ -184,6 +185,12 @@ def nb_destroy(ctx):
 
 def nb_set_params(ctx, eps, eta, dt_min, dt_max):
     _check(lib().nb_set_params(ctx, eps, eta, dt_min, dt_max), "nb_set_params")
+
+
+def nb_get_params(ctx):
+    vals = [_d() for _ in range(4)]
+    _check(lib().nb_get_params(ctx, *[ctypes.byref(x) for x in vals]), "nb_get_params")
+    return dict(zip(("eps", "eta", "dt_min", "dt_max"), (x.value for x in vals)))
 
 
 def nb_set_precision(ctx, precision):

@@ -286,3 +286,41 @@ def test_resident_order_round_trip(nbl):
         s.set_n(N - 10)
         st3 = s.get_particles(0, N - 10)
         assert np.array_equal(st3["m"], m[: N - 10]) and np.array_equal(st3["x"][100:200], x2)
+
+
+def test_snapshot_file_resume_bitwise(nbl, tmp_path):
+    # the binary snapshot holds what the block-step loop needs: an FP64 run
+    # resumed from the file repeats the uninterrupted run bit for bit
+    from paper_0709_4552_gb300 import snapshot
+    N, eps = 700, 1 / 256
+    m, x, v = inputs.plummer(N, 208, "salpeter")
+    path = tmp_path / "mid.nbs"
+    with _ctx(nbl, m, x, v, eps, 0.01, 2.0 ** -22, 2.0 ** -4) as s:
+        for _ in range(25):
+            s.step()
+        snapshot.save(s, path)
+        for _ in range(25):
+            s.step()
+        ref = _state(s, N)
+    with nbl.NBody(N, nbl.NB_FP64, 0) as s:
+        _, prm = snapshot.load(s, path)
+        assert prm["eps"] == eps and prm["dt_max"] == 2.0 ** -4
+        assert s.get_params() == dict(eps=eps, eta=0.01, dt_min=2.0 ** -22, dt_max=2.0 ** -4)
+        for _ in range(25):
+            s.step()
+        got = _state(s, N)
+    for k in ("x", "v", "a", "jerk", "t", "dt"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_invalid_parameters_rejected(nbl):
+    with nbl.NBody(16, nbl.NB_MIXED, 0) as s:
+        for bad in ((-1.0, 0.01, 2.0 ** -22, 2.0 ** -3), (0.01, 0.0, 2.0 ** -22, 2.0 ** -3),
+                    (0.01, 0.01, 3e-7, 2.0 ** -3), (0.01, 0.01, 2.0 ** -3, 2.0 ** -22),
+                    (float("nan"), 0.01, 2.0 ** -22, 2.0 ** -3)):
+            with pytest.raises(nbl.NBodyError) as e:
+                s.set_params(*bad)
+            assert e.value.code == nbl.NB_EINVAL
+        s.clear_error()
+        with pytest.raises(nbl.NBodyError):
+            s.set_j_particles(0, np.ones(3), np.array([[0.0, 0, 0], [np.inf, 0, 0], [1, 1, 1]]), np.zeros((3, 3)))
