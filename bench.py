@@ -669,7 +669,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 pairwise + f64 accumulate" if prec == nb.NB_MIXED else "f64",
+            "dtype": "f32 pairwise (packed x2) + double-single f32 accumulate" if prec == nb.NB_MIXED else "f64",
             "data": "synthetic (seeded Plummer sphere, Aarseth-Henon-Wielen sampling)",
             "config": dict(workload_config(args), parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU"),
             "gflops_60": value * FLOP_PER_INTERACTION / 1e9,

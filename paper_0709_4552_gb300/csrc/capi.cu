@@ -276,6 +276,8 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
 
 }  // namespace
 
+int nb_ensure_sorted(nb_ctx* c) { return ensure_sorted(c); }
+
 // the force dispatcher used by every entry point
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
   const nb_tuning cfg = pick_tuning(c, n);

@@ -38,6 +38,7 @@ constexpr int64_t kMaxIters = 50000000;                  // hard cap on loop ite
 struct BParams {
   double t_end, eta, dt_min, dt_max;
   int64_t max_iters;
+  int64_t seg_iters;  // > 0: stop after this many block steps of this launch (ctrl[3] = 1)
 };
 
 struct Batch {
@@ -61,6 +62,7 @@ struct Batch {
   int32_t* nsplit = nullptr;       // [C]
   int64_t* jps = nullptr;          // [C] j per split
   int64_t* item_off = nullptr;     // [C+1]
+  int64_t* ritem_off = nullptr;    // [C+1] split-reduction items (32 positions) per cluster
   int64_t* part_off = nullptr;     // [C]
   int64_t* pstride = nullptr;      // [C]
   int64_t* ctrl = nullptr;         // [4]: any active, iterations, interactions (as int64), spare
@@ -220,7 +222,7 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
                        int per_cta, int jtile, int64_t target_items, int64_t part_cap,
                        int32_t* __restrict__ itiles, int32_t* __restrict__ nsplit, int64_t* __restrict__ jps,
                        int64_t* __restrict__ item_off, int64_t* __restrict__ part_off,
-                       int64_t* __restrict__ pstride, int64_t* __restrict__ ctrl,
+                       int64_t* __restrict__ pstride, int64_t* __restrict__ ritem_off, int64_t* __restrict__ ctrl,
                        const BParams* __restrict__ prm, nb_dev_status* __restrict__ st,
                        cudaGraphConditionalHandle handle, int use_handle) {
   __shared__ int64_t sh[1024];
@@ -249,10 +251,10 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
   __syncthreads();
   for (int attempt = 0; attempt < 40; ++attempt) {
     const int64_t L = s_L;
-    int64_t item_carry = 0, part_carry = 0;
+    int64_t item_carry = 0, part_carry = 0, ritem_carry = 0;
     for (int c0 = 0; c0 < C; c0 += blockDim.x) {
       const int c = c0 + t;
-      int64_t items = 0, psz = 0;
+      int64_t items = 0, psz = 0, ritems = 0;
       int32_t it = 0, ns = 1;
       int64_t jp = 0, ps = 0;
       if (c < C) {
@@ -270,10 +272,12 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
         ps = ((n + 31) / 32) * 32;
         items = (int64_t)it * s;
         psz = s > 1 ? 7 * s * ps : 0;
+        ritems = s > 1 ? (n + 31) / 32 : 0;
       }
-      int64_t tot_items, tot_part;
+      int64_t tot_items, tot_part, tot_ritems;
       const int64_t ex_items = block_excl_scan(items, sh, &tot_items);
       const int64_t ex_part = block_excl_scan(psz, sh, &tot_part);
+      const int64_t ex_ritems = block_excl_scan(ritems, sh, &tot_ritems);
       if (c < C) {
         itiles[c] = it;
         nsplit[c] = ns;
@@ -281,12 +285,15 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
         pstride[c] = ps;
         item_off[c] = item_carry + ex_items;
         part_off[c] = part_carry + ex_part;
+        ritem_off[c] = ritem_carry + ex_ritems;
       }
       item_carry += tot_items;
       part_carry += tot_part;
+      ritem_carry += tot_ritems;
     }
     if (t == 0) {
       item_off[C] = item_carry;
+      ritem_off[C] = ritem_carry;
       s_retry = part_carry > part_cap;
       if (s_retry) s_L = s_L * 2;
     }
@@ -302,10 +309,15 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
       atomicOr(&st->flags, NB_ST_TIMEOUT);
       go = 0;
     }
+    if (go && prm->seg_iters > 0 && iters >= prm->seg_iters) {
+      ctrl[3] = 1;  // this step runs; the launch ends after it with work left
+      go = 0;
+    }
     if (s_retry) {  // partial sums do not fit: stop with an error instead of overflowing
       atomicOr(&st->flags, NB_ST_TIMEOUT);
       go = 0;
       item_off[C] = 0;
+      ritem_off[C] = 0;
     }
     ctrl[0] = go;
     if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
@@ -369,14 +381,20 @@ __device__ __forceinline__ int find_cluster(const int64_t* __restrict__ item_off
   return lo;
 }
 
+// resident CTAs per SM asked of the register allocator: the host-launched
+// mixed kernel fits 94 registers (5 CTAs of 128); the item loop must not
+// cost a CTA per SM (117 registers unbounded = 4 CTAs of 128).  The FP64
+// item keeps the default (bounding it to 96 registers spills).
+constexpr int mixed_min_ctas(int nt) { return nt >= 128 ? 5 : 20; }
+
 template <int NT, int IPT, int JT>
-__global__ void __launch_bounds__(NT) b_force_mixed(
+__global__ void __launch_bounds__(NT, mixed_min_ctas(NT)) b_force_mixed(
     int32_t C, const int64_t* __restrict__ off, const float* __restrict__ eps2f, int64_t n_pad,
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
     const int32_t* __restrict__ act, const int32_t* __restrict__ nact, const int32_t* __restrict__ itiles,
     const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
     const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
-    int64_t fstride, double* __restrict__ part) {
+    int64_t fstride, double* __restrict__ part, const float4* __restrict__ tbox) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   const int64_t total = item_off[C];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
@@ -389,7 +407,7 @@ __global__ void __launch_bounds__(NT) b_force_mixed(
     const bool fin = nsplit[c] == 1;
     double* out = fin ? F + off[c] : part + part_off[c] + split * 7 * pstride[c];
     nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_pad, act + off[c], nact[c], itile * (NT * IPT),
-                                 eps2f[c], out, fin ? fstride : pstride[c], fin);
+                                 eps2f[c], out, fin ? fstride : pstride[c], fin, tbox);
   }
 }
 
@@ -418,26 +436,26 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
 }
 
 // split-j reduction per cluster, fixed order over splits
-// split-j reduction of the active clusters: block (c, y) = cluster c,
-// positions y*32 + 32*gridDim.y*q; 32 positions x kRedLanes split lanes; lane
-// y sums splits y, y + kRedLanes, ... in order and a fixed binary tree
-// combines the lanes (one summation order per split count).  Clusters with
-// one split wrote their results directly and leave at once.
+// split-j reduction of the active clusters: one item = 32 consecutive
+// positions of one cluster with splits (item list from b_plan); block = 32
+// positions x kRedLanes split lanes; lane y sums splits y, y + kRedLanes, ...
+// in order and a fixed binary tree combines the lanes, row by row (one
+// summation order per split count).  Clusters with one split wrote their
+// results directly and have no items.
 constexpr int kRedLanes = 8;
-constexpr int kRedChunks = 16;  // blocks per cluster
-__global__ void b_reduce(const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
+__global__ void b_reduce(int32_t C, const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
                          const int32_t* __restrict__ nsplit, const int64_t* __restrict__ part_off,
-                         const int64_t* __restrict__ pstride, const double* __restrict__ part,
-                         double* __restrict__ F, int64_t fstride) {
+                         const int64_t* __restrict__ pstride, const int64_t* __restrict__ ritem_off,
+                         const double* __restrict__ part, double* __restrict__ F, int64_t fstride) {
   __shared__ double sm[kRedLanes][33];
-  const int c = blockIdx.x;
-  const int S = nsplit[c];
-  if (S <= 1) return;  // uniform over the block
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t n = nact[c], o = off[c], ps = pstride[c];
-  const double* p = part + part_off[c];
-  for (int64_t k0 = (int64_t)blockIdx.y * 32; k0 < n; k0 += (int64_t)gridDim.y * 32) {
-    const int64_t k = k0 + tx;
+  const int64_t total = ritem_off[C];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_cluster(ritem_off, C, item);
+    const int S = nsplit[c];
+    const int64_t n = nact[c], o = off[c], ps = pstride[c];
+    const double* p = part + part_off[c];
+    const int64_t k = (item - ritem_off[c]) * 32 + tx;
     for (int r = 0; r < 7; ++r) {
       double acc = 0.0;
       if (k < n)
@@ -601,8 +619,8 @@ int grid_for(int64_t n, int threads, int cap) {
 void batch_free(Batch* b) {
   if (!b) return;
   void* p[] = {b->off, b->eps2f, b->eps2d, b->cid, b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min,
-               b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
-               b->ctrl, b->prm, b->esum};
+               b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->ritem_off, b->part_off,
+               b->pstride, b->ctrl, b->prm, b->esum};
   for (void* q : p)
     if (q) cudaFree(q);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -653,7 +671,7 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   BA(b->off, C + 1) BA(b->eps2f, C) BA(b->eps2d, C) BA(b->cid, c->n_pad) BA(b->ch_cluster, b->nchunks)
   BA(b->ch_lo, b->nchunks) BA(b->ch_hi, b->nchunks) BA(b->cl_ch0, C + 1) BA(b->ch_min, b->nchunks)
   BA(b->ch_cnt, b->nchunks) BA(b->tnext, C) BA(b->nact, C) BA(b->itiles, C) BA(b->nsplit, C) BA(b->jps, C)
-  BA(b->item_off, C + 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
+  BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
 #undef BA
   auto H2D = [&](void* d, const void* h, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream);
@@ -689,12 +707,15 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   return cudaSuccess;
 }
 
-cudaError_t set_params(nb_ctx* c, Batch* b, double t_end) {
-  // every block step moves the earliest particle forward by at least dt_min,
-  // so no run can need more than t_end / dt_min + 2 loop iterations
+// every block step moves the earliest particle forward by at least dt_min,
+// so no run can need more than t_end / dt_min + 2 loop iterations
+int64_t iteration_cap(const nb_ctx* c, double t_end) {
   int64_t cap = (int64_t)ceil(t_end / c->dt_min) + 2;
-  if (cap > kMaxIters) cap = kMaxIters;
-  BParams p{t_end, c->eta, c->dt_min, c->dt_max, cap};
+  return cap > kMaxIters ? kMaxIters : cap;
+}
+
+cudaError_t set_params(nb_ctx* c, Batch* b, double t_end, int64_t seg_iters = 0) {
+  BParams p{t_end, c->eta, c->dt_min, c->dt_max, iteration_cap(c, t_end), seg_iters};
   // pinned staging keeps the copy asynchronous-safe
   memcpy(c->hpin, &p, sizeof(p));
   cudaError_t e = cudaMemcpyAsync(b->prm, c->hpin, sizeof(p), cudaMemcpyHostToDevice, c->stream);
@@ -709,9 +730,16 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const int jt = mixed ? kMixJT : kF64JT;
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
-                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride, b->ctrl,
+                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
+                                    b->ritem_off, b->ctrl,
                                     b->prm, c->status, 0, 0);
   return cudaGetLastError();
+}
+
+// a single system's j-ranges start at row 0 in multiples of the j-tile, so
+// the 128-row tile boxes of the spatial order line up with its tiles
+bool single_boxes(const nb_ctx* c, const Batch* b) {
+  return c->precision == NB_MIXED && c->n_clusters == 0 && b->C == 1;
 }
 
 template <int NT>
@@ -719,7 +747,7 @@ void launch_force(nb_ctx* c, Batch* b, bool mixed) {
   if (mixed)
     b_force_mixed<NT, kMixIPT, kMixJT><<<b->grid_mixed, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part, single_boxes(c, b) ? c->tbox : nullptr);
   else
     b_force_fp64<NT, kF64JT><<<b->grid_fp64, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
@@ -731,12 +759,16 @@ cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
   const int g = grid_for(b->N, 256, c->sm_count * 16);
   b_predict<<<g, 256, 0, c->stream>>>(b->N, c->n_pad, b->cid, b->nact, b->tnext, own_time ? 1 : 0, c->m, c->x,
                                       c->v, c->a, c->jk, c->t, c->xp, c->vp, c->jA, c->jB, c->jC, 1, mixed ? 1 : 0);
+  if (single_boxes(c, b)) {
+    cudaError_t e = nb_launch_tile_boxes(c);  // boxes of the predicted tiles for the far test
+    if (e != cudaSuccess) return e;
+  }
   if (b->nt == 32)
     launch_force<32>(c, b, mixed);
   else
     launch_force<128>(c, b, mixed);
-  b_reduce<<<dim3((unsigned)b->C, kRedChunks), dim3(32, kRedLanes), 0, c->stream>>>(
-      b->off, b->nact, b->nsplit, b->part_off, b->pstride, c->part, c->F, c->n_pad);
+  b_reduce<<<c->sm_count * 8, dim3(32, kRedLanes), 0, c->stream>>>(
+      b->C, b->off, b->nact, b->nsplit, b->part_off, b->pstride, b->ritem_off, c->part, c->F, c->n_pad);
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -753,7 +785,8 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
   b_sel_write<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_cnt, b->off,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
-                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride, b->ctrl,
+                                    b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
+                                    b->ritem_off, b->ctrl,
                                     b->prm, c->status, handle, use_handle);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -831,20 +864,40 @@ int64_t read_ctrl(nb_ctx* c, Batch* b, int idx) {
   return v;
 }
 
-// graph-driven integration of every cluster of b to t_end
+// graph-driven integration of every cluster of b to t_end.  A single mixed
+// system keeps its resident spatial order: the graph runs in segments of at
+// most sort_interval block steps, and the order is renewed between them.
 int run_graph(nb_ctx* c, Batch* b, double t_end) {
-  if (set_params(c, b, t_end) != cudaSuccess) return NB_ECUDA;
   if (build_graph(c, b) != cudaSuccess) {
     cudaGetLastError();
     return NB_ECUDA;
   }
-  if (cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream) != cudaSuccess) return NB_ECUDA;
-  if (cudaGraphLaunch(b->exec, c->stream) != cudaSuccess) return NB_ECUDA;
-  const int64_t iters = read_ctrl(c, b, 1);
-  const int64_t inter = read_ctrl(c, b, 2);
-  c->steps += iters > 0 ? iters - 1 : 0;
-  c->interactions += (double)inter;
-  c->launches += iters * 8;
+  const bool seg = single_boxes(c, b);
+  const int64_t cap = iteration_cap(c, t_end);
+  int64_t total = 0;
+  for (;;) {
+    int64_t seg_iters = 0;
+    if (seg) {
+      const int rs = nb_ensure_sorted(c);
+      if (rs != NB_OK) return rs;
+      seg_iters = std::max(1, c->sort_interval - c->perm_age);
+    }
+    if (set_params(c, b, t_end, seg_iters) != cudaSuccess) return NB_ECUDA;
+    if (cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream) != cudaSuccess) return NB_ECUDA;
+    if (cudaGraphLaunch(b->exec, c->stream) != cudaSuccess) return NB_ECUDA;
+    const int64_t iters = read_ctrl(c, b, 1);
+    const int64_t inter = read_ctrl(c, b, 2);
+    const bool more = read_ctrl(c, b, 3) != 0;
+    // a finished run ends with one iteration that selects nothing
+    const int64_t steps = more ? iters : (iters > 0 ? iters - 1 : 0);
+    c->steps += steps;
+    c->perm_age += (int)steps;
+    c->interactions += (double)inter;
+    c->launches += iters * (seg ? 9 : 8);
+    total += iters;
+    if (!more) break;
+    if (total > cap) return NB_ETIMEOUT;  // cannot happen for valid block steps
+  }
   c->pred_valid = false;
   c->f_valid = false;
   return finish_status(c);

@@ -18,8 +18,10 @@
 // a pair is formed completely before it is accumulated: its two parts
 // (w / s^3 and -3 (r.w) r / s^5) cancel for close pairs, and adding them to
 // the running sum one after the other costs up to 4x in the worst particle's
-// error.  FP32 partial sums over one j-tile (JT pairs) are folded into FP64
-// accumulators.  j-tiles (40 B per particle: float4
+// error.  FP32 partial sums over one j-tile (JT pairs) are folded into
+// double-single accumulators (an FP32 pair hi + lo, Knuth's TwoSum: no FP64
+// instruction in the loop; NB_MIXED_DS_FOLD = 0 folds into FP64 instead).
+// j-tiles (40 B per particle: float4
 // hi+m, float4 lo+vx, float2 vy vz) are staged in shared memory with cp.async
 // double buffering and read as warp-wide broadcasts.
 //
@@ -47,9 +49,9 @@
 #ifndef NB_MIXED_SMEM_ACC
 #define NB_MIXED_SMEM_ACC 0
 #endif
-// double-single (FP32 TwoSum) accumulators instead of FP64 in the mixed path
+// double-single (FP32 TwoSum) accumulators of the mixed path (0 = FP64)
 #ifndef NB_MIXED_DS_FOLD
-#define NB_MIXED_DS_FOLD 0
+#define NB_MIXED_DS_FOLD 1
 #endif
 // unroll depth of the mixed inner loop over a j-tile
 #ifndef NB_MIXED_UNROLL

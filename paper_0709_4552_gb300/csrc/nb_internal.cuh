@@ -174,6 +174,9 @@ cudaError_t nb_launch_tile_boxes(nb_ctx* c);  // tbox from the predicted (permut
 // processing order of a list of slots: positions sorted by slot (device array of n positions)
 cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord);
 
+// capi.cu: (re)compute the resident spatial order when it is due (mixed path)
+int nb_ensure_sorted(nb_ctx* c);
+
 // ensemble.cu
 void nb_ensemble_free(nb_ctx* c);
 int nb_integrate_graph(nb_ctx* c, double t_end);
