@@ -63,6 +63,7 @@ struct Batch {
   int64_t* jps = nullptr;          // [C] j per split
   int64_t* item_off = nullptr;     // [C+1]
   int64_t* ritem_off = nullptr;    // [C+1] split-reduction items (32 positions) per cluster
+  unsigned long long* wq = nullptr;  // force-item counter of the current step
   int64_t* part_off = nullptr;     // [C]
   int64_t* pstride = nullptr;      // [C]
   int64_t* ctrl = nullptr;         // [4]: any active, iterations, interactions (as int64), spare
@@ -222,7 +223,8 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
                        int per_cta, int jtile, int64_t target_items, int64_t part_cap,
                        int32_t* __restrict__ itiles, int32_t* __restrict__ nsplit, int64_t* __restrict__ jps,
                        int64_t* __restrict__ item_off, int64_t* __restrict__ part_off,
-                       int64_t* __restrict__ pstride, int64_t* __restrict__ ritem_off, int64_t* __restrict__ ctrl,
+                       int64_t* __restrict__ pstride, int64_t* __restrict__ ritem_off,
+                       unsigned long long* __restrict__ wq, int64_t* __restrict__ ctrl,
                        const BParams* __restrict__ prm, nb_dev_status* __restrict__ st,
                        cudaGraphConditionalHandle handle, int use_handle) {
   __shared__ int64_t sh[1024];
@@ -301,6 +303,7 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
     if (!s_retry) break;
   }
   if (t == 0) {
+    *wq = 0;  // the force kernel of this step starts at item 0
     int64_t iters = ctrl[1] + 1;
     ctrl[1] = iters;
     ctrl[2] += tot_i;
@@ -381,6 +384,17 @@ __device__ __forceinline__ int find_cluster(const int64_t* __restrict__ item_off
   return lo;
 }
 
+// the next force item for this CTA from the step's work counter (reset by
+// b_plan): items go to whichever CTA is free first, so uneven items (near or
+// far tiles, big or small clusters) do not leave SMs idle at the end of a
+// step.  One atomic per item; no waiting.
+__device__ __forceinline__ int64_t next_item(unsigned long long* wq, int64_t* s_item) {
+  __syncthreads();  // every thread has read the previous item
+  if (threadIdx.x == 0) *s_item = (int64_t)atomicAdd(wq, 1ULL);
+  __syncthreads();
+  return *s_item;
+}
+
 // resident CTAs per SM asked of the register allocator: the host-launched
 // mixed kernel fits 94 registers (5 CTAs of 128); the item loop must not
 // cost a CTA per SM (117 registers unbounded = 4 CTAs of 128).  The FP64
@@ -394,10 +408,14 @@ __global__ void __launch_bounds__(NT, mixed_min_ctas(NT)) b_force_mixed(
     const int32_t* __restrict__ act, const int32_t* __restrict__ nact, const int32_t* __restrict__ itiles,
     const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
     const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
-    int64_t fstride, double* __restrict__ part, const float4* __restrict__ tbox) {
+    int64_t fstride, double* __restrict__ part, const float4* __restrict__ tbox,
+    unsigned long long* __restrict__ wq) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
+  __shared__ int64_t s_item;
   const int64_t total = item_off[C];
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+  for (;;) {
+    const int64_t item = next_item(wq, &s_item);
+    if (item >= total) break;
     const int c = find_cluster(item_off, C, item);
     const int64_t local = item - item_off[c];
     const int it = itiles[c];
@@ -418,10 +436,13 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
     const int32_t* __restrict__ act, const int32_t* __restrict__ nact, const int32_t* __restrict__ itiles,
     const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
     const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
-    int64_t fstride, double* __restrict__ part) {
+    int64_t fstride, double* __restrict__ part, unsigned long long* __restrict__ wq) {
   __shared__ nbk::Fp64Smem<JT> sm;
+  __shared__ int64_t s_item;
   const int64_t total = item_off[C];
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+  for (;;) {
+    const int64_t item = next_item(wq, &s_item);
+    if (item >= total) break;
     const int c = find_cluster(item_off, C, item);
     const int64_t local = item - item_off[c];
     const int it = itiles[c];
@@ -435,7 +456,6 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
   }
 }
 
-// split-j reduction per cluster, fixed order over splits
 // split-j reduction of the active clusters: one item = 32 consecutive
 // positions of one cluster with splits (item list from b_plan); block = 32
 // positions x kRedLanes split lanes; lane y sums splits y, y + kRedLanes, ...
@@ -620,7 +640,7 @@ void batch_free(Batch* b) {
   if (!b) return;
   void* p[] = {b->off, b->eps2f, b->eps2d, b->cid, b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min,
                b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->ritem_off, b->part_off,
-               b->pstride, b->ctrl, b->prm, b->esum};
+               b->pstride, b->ctrl, b->prm, b->esum, b->wq};
   for (void* q : p)
     if (q) cudaFree(q);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -671,7 +691,7 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   BA(b->off, C + 1) BA(b->eps2f, C) BA(b->eps2d, C) BA(b->cid, c->n_pad) BA(b->ch_cluster, b->nchunks)
   BA(b->ch_lo, b->nchunks) BA(b->ch_hi, b->nchunks) BA(b->cl_ch0, C + 1) BA(b->ch_min, b->nchunks)
   BA(b->ch_cnt, b->nchunks) BA(b->tnext, C) BA(b->nact, C) BA(b->itiles, C) BA(b->nsplit, C) BA(b->jps, C)
-  BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
+  BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->wq, 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
 #undef BA
   auto H2D = [&](void* d, const void* h, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream);
@@ -731,7 +751,7 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
-                                    b->ritem_off, b->ctrl,
+                                    b->ritem_off, b->wq, b->ctrl,
                                     b->prm, c->status, 0, 0);
   return cudaGetLastError();
 }
@@ -747,11 +767,12 @@ void launch_force(nb_ctx* c, Batch* b, bool mixed) {
   if (mixed)
     b_force_mixed<NT, kMixIPT, kMixJT><<<b->grid_mixed, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part, single_boxes(c, b) ? c->tbox : nullptr);
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part, single_boxes(c, b) ? c->tbox : nullptr,
+        b->wq);
   else
     b_force_fp64<NT, kF64JT><<<b->grid_fp64, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part);
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part, b->wq);
 }
 
 cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
@@ -786,7 +807,7 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
-                                    b->ritem_off, b->ctrl,
+                                    b->ritem_off, b->wq, b->ctrl,
                                     b->prm, c->status, handle, use_handle);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
