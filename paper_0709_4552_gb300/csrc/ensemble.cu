@@ -26,7 +26,11 @@
 
 namespace {
 
-constexpr int kSelChunk = 2048;   // particles per selection chunk (chunks never straddle clusters)
+#ifndef NB_ENS_ITEM_WAVES
+#define NB_ENS_ITEM_WAVES 4
+#endif
+constexpr int kItemWaves = NB_ENS_ITEM_WAVES;  // force items planned per resident CTA
+constexpr int kSelChunk = 512;    // particles per selection chunk (chunks never straddle clusters)
 // batched item shapes: i-tile = threads per CTA, one i per thread.  An
 // ensemble of small clusters has small active blocks (n = 0.20 N^0.81 is 18
 // at N = 256 and 169 at N = 4096), so it takes 32-particle i-tiles that
@@ -110,9 +114,16 @@ __global__ void b_sel_min(const int64_t* __restrict__ lo, const int64_t* __restr
   }
 }
 
+// the cluster's block time: minimum over its chunks, by the calling warp
+// (every lane returns it)
 __device__ __forceinline__ double cluster_tmin(const unsigned long long* ch_min, int a, int b) {
+  const int lane = threadIdx.x & 31;
   unsigned long long best = 0x7FF0000000000000ULL;
-  for (int q = a; q < b; ++q) best = ch_min[q] < best ? ch_min[q] : best;
+  for (int q = a + lane; q < b; q += 32) best = ch_min[q] < best ? ch_min[q] : best;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+    best = w < best ? w : best;
+  }
   return __longlong_as_double((long long)best);
 }
 
@@ -124,9 +135,12 @@ __global__ void b_sel_count(const int32_t* __restrict__ ch_cluster, const int64_
   const int j = blockIdx.x;
   const int c = ch_cluster[j];
   __shared__ double tn;
-  if (threadIdx.x == 0) {
-    tn = cluster_tmin(ch_min, cl_ch0[c], cl_ch0[c + 1]);
-    if (j == cl_ch0[c]) tnext[c] = tn;
+  if (threadIdx.x < 32) {
+    const double t = cluster_tmin(ch_min, cl_ch0[c], cl_ch0[c + 1]);
+    if (threadIdx.x == 0) {
+      tn = t;
+      if (j == cl_ch0[c]) tnext[c] = t;
+    }
   }
   __syncthreads();
   int cnt = 0;
@@ -152,14 +166,20 @@ __global__ void b_sel_write(const int32_t* __restrict__ ch_cluster, const int64_
   const int c = ch_cluster[j];
   const double tn = tnext[c];
   __shared__ int base_s;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // counts of the cluster's chunks before this one, and in all
     int b = 0, tot = 0;
-    for (int q = cl_ch0[c]; q < cl_ch0[c + 1]; ++q) {
+    for (int q = cl_ch0[c] + (int)threadIdx.x; q < cl_ch0[c + 1]; q += 32) {
       if (q < j) b += ch_cnt[q];
       tot += ch_cnt[q];
     }
-    base_s = b;
-    if (j == cl_ch0[c]) nact[c] = (tn <= prm->t_end) ? tot : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (threadIdx.x == 0) {
+      base_s = b;
+      if (j == cl_ch0[c]) nact[c] = (tn <= prm->t_end) ? tot : 0;
+    }
   }
   __syncthreads();
   int base = (int)off[c] + base_s;
@@ -274,7 +294,7 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
         ps = ((n + 31) / 32) * 32;
         items = (int64_t)it * s;
         psz = s > 1 ? 7 * s * ps : 0;
-        ritems = s > 1 ? (n + 31) / 32 : 0;
+        ritems = s > 1 ? 7 * ((n + 31) / 32) : 0;
       }
       int64_t tot_items, tot_part, tot_ritems;
       const int64_t ex_items = block_excl_scan(items, sh, &tot_items);
@@ -456,13 +476,16 @@ __global__ void __launch_bounds__(NT) b_force_fp64(
   }
 }
 
-// split-j reduction of the active clusters: one item = 32 consecutive
-// positions of one cluster with splits (item list from b_plan); block = 32
-// positions x kRedLanes split lanes; lane y sums splits y, y + kRedLanes, ...
-// in order and a fixed binary tree combines the lanes, row by row (one
-// summation order per split count).  Clusters with one split wrote their
+// split-j reduction of the active clusters: one item = one of the 7 result
+// rows of 32 consecutive positions of one cluster with splits (item list from
+// b_plan); block = 32 positions x kRedLanes split lanes; lane y sums splits
+// y, y + kRedLanes, ... in order and a fixed binary tree combines the lanes
+// (one summation order per split count).  Clusters with one split wrote their
 // results directly and have no items.
-constexpr int kRedLanes = 8;
+#ifndef NB_ENS_RED_LANES
+#define NB_ENS_RED_LANES 8
+#endif
+constexpr int kRedLanes = NB_ENS_RED_LANES;
 __global__ void b_reduce(int32_t C, const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
                          const int32_t* __restrict__ nsplit, const int64_t* __restrict__ part_off,
                          const int64_t* __restrict__ pstride, const int64_t* __restrict__ ritem_off,
@@ -475,21 +498,21 @@ __global__ void b_reduce(int32_t C, const int64_t* __restrict__ off, const int32
     const int S = nsplit[c];
     const int64_t n = nact[c], o = off[c], ps = pstride[c];
     const double* p = part + part_off[c];
-    const int64_t k = (item - ritem_off[c]) * 32 + tx;
-    for (int r = 0; r < 7; ++r) {
-      double acc = 0.0;
-      if (k < n)
-        for (int q = ty; q < S; q += kRedLanes) acc += p[((int64_t)q * 7 + r) * ps + k];
-      sm[ty][tx] = acc;
-      __syncthreads();
+    const int64_t local = item - ritem_off[c];
+    const int r = (int)(local % 7);
+    const int64_t k = (local / 7) * 32 + tx;
+    double acc = 0.0;
+    if (k < n)
+      for (int q = ty; q < S; q += kRedLanes) acc += p[((int64_t)q * 7 + r) * ps + k];
+    sm[ty][tx] = acc;
+    __syncthreads();
 #pragma unroll
-      for (int h = kRedLanes / 2; h > 0; h >>= 1) {
-        if (ty < h) sm[ty][tx] += sm[ty + h][tx];
-        __syncthreads();
-      }
-      if (ty == 0 && k < n) F[r * fstride + o + k] = r == 6 ? -sm[0][tx] : sm[0][tx];
+    for (int h = kRedLanes / 2; h > 0; h >>= 1) {
+      if (ty < h) sm[ty][tx] += sm[ty + h][tx];
       __syncthreads();
     }
+    if (ty == 0 && k < n) F[r * fstride + o + k] = r == 6 ? -sm[0][tx] : sm[0][tx];
+    __syncthreads();
   }
 }
 
@@ -749,7 +772,7 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const int per_cta = b->nt * (mixed ? kMixIPT : 1);
   const int jt = mixed ? kMixJT : kF64JT;
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
-  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
                                     b->ritem_off, b->wq, b->ctrl,
                                     b->prm, c->status, 0, 0);
@@ -805,7 +828,7 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
                                                  c->dt, b->tnext, b->ch_cnt);
   b_sel_write<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_cnt, b->off,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
-  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, 4 * (int64_t)grid, c->part_elems,
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
                                     b->ritem_off, b->wq, b->ctrl,
                                     b->prm, c->status, handle, use_handle);

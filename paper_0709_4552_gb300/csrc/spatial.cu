@@ -54,16 +54,27 @@ __global__ void bbox_partial(int64_t N, int64_t n_pad, const double* __restrict_
   if (threadIdx.x < 6) red[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void bbox_final(int nb, double* __restrict__ red, double* __restrict__ out) {
-  if (threadIdx.x == 0) {
-    double b[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int k = 0; k < nb; ++k)
+// one CTA of kSortThreads: strided partial minima/maxima, then a tree (min
+// and max are exact, so the order does not matter)
+__global__ void bbox_final(int nb, const double* __restrict__ red, double* __restrict__ out) {
+  double b[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int k = threadIdx.x; k < nb; k += blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      b[c] = fmin(b[c], red[k * 6 + c]);
+      b[3 + c] = fmax(b[3 + c], red[k * 6 + 3 + c]);
+    }
+  __shared__ double s[6][kSortThreads];
+  for (int c = 0; c < 6; ++c) s[c][threadIdx.x] = b[c];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
       for (int c = 0; c < 3; ++c) {
-        b[c] = fmin(b[c], red[k * 6 + c]);
-        b[3 + c] = fmax(b[3 + c], red[k * 6 + 3 + c]);
+        s[c][threadIdx.x] = fmin(s[c][threadIdx.x], s[c][threadIdx.x + w]);
+        s[3 + c][threadIdx.x] = fmax(s[3 + c][threadIdx.x], s[3 + c][threadIdx.x + w]);
       }
-    for (int c = 0; c < 6; ++c) out[c] = b[c];
+    __syncthreads();
   }
+  if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
 __device__ __forceinline__ uint32_t spread10(uint32_t a) {  // 10 bits -> every third bit
@@ -322,7 +333,7 @@ cudaError_t nb_spatial_sort(nb_ctx* c) {
   const int nbb = grid_for(N, kSortThreads, 1024);
   double* box = c->red + NB_BBOX_OFFSET;
   bbox_partial<<<nbb, kSortThreads, 0, c->stream>>>(N, c->n_pad, c->x, c->red);
-  bbox_final<<<1, 32, 0, c->stream>>>(nbb, c->red, box);
+  bbox_final<<<1, kSortThreads, 0, c->stream>>>(nbb, c->red, box);
   morton_keys<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->n_pad, c->x, box, c->skey[0],
                                                                          c->sval[0]);
   int cur = 0;
