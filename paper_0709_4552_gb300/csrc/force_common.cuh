@@ -153,11 +153,16 @@ __device__ __forceinline__ void mixed_load_tile_pairs(float4* sA, float4* sB, fl
 // One j-tile against the thread's IPT i-particles; FP32 partials in p.
 // MODE: kFar  -- the tile is far from every i of the warp: hi parts alone
 //                (r = x_j.hi - x_i.hi, within 2^-24 (|x_i|+|x_j|) of the exact
-//                difference, i.e. FP32 accuracy at the far-test distance);
+//                difference: relative error <= 2^-24 (1/theta + 1) at the
+//                far-test distance);
 //       kNear -- double-single difference;
 //       kSelf -- double-single difference, pairs with j == i get 1/s = 0.
 constexpr int kFar = 0, kNear = 1, kSelf = 2;
-constexpr float kFarTheta = 0.25f;  // far test: box gap >= theta * (|x|max_i + |x|max_j)
+// far test: box gap >= theta * (|x|max_i + |x|max_j)
+#ifndef NB_FAR_THETA
+#define NB_FAR_THETA 0.125f
+#endif
+constexpr float kFarTheta = NB_FAR_THETA;
 
 template <int IPT, int JT, int MODE>
 __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, const float4* __restrict__ sB,
