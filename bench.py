@@ -223,7 +223,8 @@ def workload_config(args):
     return {"workload": f"Plummer sphere N={args.n}, equal masses, eps=1/{round(1 / args.eps)}, "
                         f"shared dt=2^-10 (every block step is a full i=j step of {args.precision} forces)",
             "N": args.n, "n_active": args.n, "eps": args.eps, "precision": args.precision, "seed": args.seed,
-            "l2": "state read per step 0.35 GB > L2 (126 MB); L2 flushed (512 MB write) between steps"}
+            "l2": f"block-step arrays {args.n * 336 / 1e9:.3g} GB (state, prediction, j-store, results); "
+                  "L2 (126 MB) flushed by a 512 MB write before every timed step"}
 
 
 def run_integration(args):
