@@ -324,3 +324,53 @@ def test_invalid_parameters_rejected(nbl):
         s.clear_error()
         with pytest.raises(nbl.NBodyError):
             s.set_j_particles(0, np.ones(3), np.array([[0.0, 0, 0], [np.inf, 0, 0], [1, 1, 1]]), np.zeros((3, 3)))
+
+
+def test_resident_order_random_api_sequence(nbl):
+    # a seeded random sequence of ABI calls on a mixed context (whose arrays
+    # are kept in spatial order): every read-back and every force result must
+    # be the one of the particles the caller names
+    N, eps = 2500, 1 / 256
+    rng = np.random.default_rng(209)
+    m, x, v = inputs.plummer(N, 209, "salpeter")
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -4)
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()
+        for it in range(12):
+            op = it % 4
+            if op == 0:          # block steps (the order is renewed every 64)
+                for _ in range(int(rng.integers(1, 40))):
+                    s.step()
+            elif op == 1:        # forces on a random caller list at the current block time
+                st = s.get_particles(0, N)
+                t, n, act = s.next_block()
+                idx = np.sort(rng.choice(N, int(rng.integers(1, N)), replace=False)).astype(np.int32)
+                s.predict(t)
+                a, j, p = s.compute_forces(idx)
+                # the oracle on the same predicted state, particle by particle
+                h = (t - st["t"])[:, None]
+                xp = st["x"] + h * (st["v"] + h * (0.5 * st["a"] + h * st["jerk"] / 6))
+                vp = st["v"] + h * (st["a"] + h * 0.5 * st["jerk"])
+                ar, jr, pr = oracle.forces(st["m"], xp, vp, eps, idx=idx.astype(np.int64))
+                assert rel_vec(a, ar).max() < 1e-5 and rel_scalar(p, pr).max() < 1e-5
+            elif op == 2:        # overwrite a random range, read everything back
+                lo = int(rng.integers(0, N - 10))
+                cnt = int(rng.integers(1, N - lo))
+                st = s.get_particles(0, N)
+                x2 = st["x"][lo:lo + cnt] + 1e-3 * rng.normal(size=(cnt, 3))
+                s.set_j_particles(lo, st["m"][lo:lo + cnt], x2, st["v"][lo:lo + cnt], st["a"][lo:lo + cnt],
+                                  st["jerk"][lo:lo + cnt], st["t"][lo:lo + cnt], st["dt"][lo:lo + cnt])
+                got = s.get_particles(0, N)
+                want = st["x"].copy()
+                want[lo:lo + cnt] = x2
+                assert np.array_equal(got["x"], want)
+                for k in ("m", "v", "t", "dt"):
+                    assert np.array_equal(got[k], st[k]), k
+            else:                # sub-range reads agree with the full read
+                st = s.get_particles(0, N)
+                lo = int(rng.integers(0, N - 1))
+                cnt = int(rng.integers(1, N - lo + 1))
+                sub = s.get_particles(lo, cnt)
+                for k in ("m", "x", "v", "a", "jerk", "t", "dt"):
+                    assert np.array_equal(sub[k], st[k][lo:lo + cnt]), k
