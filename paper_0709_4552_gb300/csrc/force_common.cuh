@@ -210,16 +210,16 @@ __device__ __forceinline__ void mixed_tile_pass(const float4* __restrict__ sA, c
   }
 }
 
-// The same pass for one i per thread on the pair layout: every FP32 operation
-// acts on the pair (j, j+1) at once (packed FP32x2 add/mul/fma, each lane
-// rounded exactly as its scalar counterpart), which halves the issue slots of
-// the FP32 work.  ni* hold the NEGATED i coordinates and velocity in both
-// lanes, so x_j + (-x_i) is the scalar x_j - x_i bit for bit.  The two lanes
-// of p sum the even and the odd j of the tile.
-template <int JT, int MODE>
-__device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const float2 (&nxh)[3],
-                                                const float2 (&nxl)[3], const float2 (&nv)[3], int rel,
-                                                float2 eps2, float2 (&p)[7]) {
+// The same pass on the pair layout for IPT i per thread: every FP32
+// operation acts on the pair (j, j+1) at once (packed FP32x2 add/mul/fma,
+// each lane rounded exactly as its scalar counterpart), which halves the
+// issue slots of the FP32 work.  ni* hold the NEGATED i coordinates and
+// velocity in both lanes, so x_j + (-x_i) is the scalar x_j - x_i bit for
+// bit.  The two lanes of p sum the even and the odd j of the tile.
+template <int IPT, int JT, int MODE>
+__device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const float2 (&nxh)[IPT][3],
+                                                const float2 (&nxl)[IPT][3], const float2 (&nv)[IPT][3],
+                                                const int (&rel)[IPT], float2 eps2, float2 (&p)[IPT][7]) {
   const float4* __restrict__ P0 = (const float4*)t.p0;
   const float4* __restrict__ P1 = (const float4*)t.p1;
   const float4* __restrict__ P2 = (const float4*)t.p2;
@@ -229,42 +229,46 @@ __device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const flo
   NB_PRAGMA_UNROLL(NB_MIXED_UNROLL)
   for (int u = 0; u < JT / 2; ++u) {
     const float4 a = P0[u], b = P1[u], c = P2[u], d = P3[u];
-    float2 dx = __fadd2_rn(make_float2(a.x, a.y), nxh[0]);
-    float2 dy = __fadd2_rn(make_float2(a.z, a.w), nxh[1]);
-    float2 dz = __fadd2_rn(make_float2(b.x, b.y), nxh[2]);
-    if (MODE != kFar) {
-      const float4 e = P4[u];
-      dx = __fadd2_rn(dx, __fadd2_rn(make_float2(d.z, d.w), nxl[0]));
-      dy = __fadd2_rn(dy, __fadd2_rn(make_float2(e.x, e.y), nxl[1]));
-      dz = __fadd2_rn(dz, __fadd2_rn(make_float2(e.z, e.w), nxl[2]));
-    }
-    const float2 wx = __fadd2_rn(make_float2(c.x, c.y), nv[0]);
-    const float2 wy = __fadd2_rn(make_float2(c.z, c.w), nv[1]);
-    const float2 wz = __fadd2_rn(make_float2(d.x, d.y), nv[2]);
-    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
-    const float2 rw = __ffma2_rn(dz, wz, __ffma2_rn(dy, wy, __fmul2_rn(dx, wx)));
+    float4 e;
+    if (MODE != kFar) e = P4[u];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      float2 dx = __fadd2_rn(make_float2(a.x, a.y), nxh[k][0]);
+      float2 dy = __fadd2_rn(make_float2(a.z, a.w), nxh[k][1]);
+      float2 dz = __fadd2_rn(make_float2(b.x, b.y), nxh[k][2]);
+      if (MODE != kFar) {
+        dx = __fadd2_rn(dx, __fadd2_rn(make_float2(d.z, d.w), nxl[k][0]));
+        dy = __fadd2_rn(dy, __fadd2_rn(make_float2(e.x, e.y), nxl[k][1]));
+        dz = __fadd2_rn(dz, __fadd2_rn(make_float2(e.z, e.w), nxl[k][2]));
+      }
+      const float2 wx = __fadd2_rn(make_float2(c.x, c.y), nv[k][0]);
+      const float2 wy = __fadd2_rn(make_float2(c.z, c.w), nv[k][1]);
+      const float2 wz = __fadd2_rn(make_float2(d.x, d.y), nv[k][2]);
+      const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+      const float2 rw = __ffma2_rn(dz, wz, __ffma2_rn(dy, wy, __fmul2_rn(dx, wx)));
 #if NB_MIXED_NEWTON
-    const float2 y0 = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
-    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), __fmul2_rn(y0, y0), make_float2(1.0f, 1.0f));
-    float2 rinv = __ffma2_rn(make_float2(0.5f, 0.5f), __fmul2_rn(y0, e), y0);
+      const float2 y0 = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
+      const float2 ee = __ffma2_rn(make_float2(-r2.x, -r2.y), __fmul2_rn(y0, y0), make_float2(1.0f, 1.0f));
+      float2 rinv = __ffma2_rn(make_float2(0.5f, 0.5f), __fmul2_rn(y0, ee), y0);
 #else
-    float2 rinv = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
+      float2 rinv = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
 #endif
-    if (MODE == kSelf) {
-      rinv.x = (2 * u == rel) ? 0.0f : rinv.x;
-      rinv.y = (2 * u + 1 == rel) ? 0.0f : rinv.y;
+      if (MODE == kSelf) {
+        rinv.x = (2 * u == rel[k]) ? 0.0f : rinv.x;
+        rinv.y = (2 * u + 1 == rel[k]) ? 0.0f : rinv.y;
+      }
+      const float2 rinv2 = __fmul2_rn(rinv, rinv);
+      const float2 mr = __fmul2_rn(make_float2(b.z, b.w), rinv);
+      const float2 mr3 = __fmul2_rn(mr, rinv2);
+      const float2 a3 = __fmul2_rn(__fmul2_rn(rw, m3), rinv2);
+      p[k][6] = __fadd2_rn(p[k][6], mr);
+      p[k][0] = __ffma2_rn(mr3, dx, p[k][0]);
+      p[k][1] = __ffma2_rn(mr3, dy, p[k][1]);
+      p[k][2] = __ffma2_rn(mr3, dz, p[k][2]);
+      p[k][3] = __ffma2_rn(mr3, __ffma2_rn(a3, dx, wx), p[k][3]);
+      p[k][4] = __ffma2_rn(mr3, __ffma2_rn(a3, dy, wy), p[k][4]);
+      p[k][5] = __ffma2_rn(mr3, __ffma2_rn(a3, dz, wz), p[k][5]);
     }
-    const float2 rinv2 = __fmul2_rn(rinv, rinv);
-    const float2 mr = __fmul2_rn(make_float2(b.z, b.w), rinv);
-    const float2 mr3 = __fmul2_rn(mr, rinv2);
-    const float2 a3 = __fmul2_rn(__fmul2_rn(rw, m3), rinv2);
-    p[6] = __fadd2_rn(p[6], mr);
-    p[0] = __ffma2_rn(mr3, dx, p[0]);
-    p[1] = __ffma2_rn(mr3, dy, p[1]);
-    p[2] = __ffma2_rn(mr3, dz, p[2]);
-    p[3] = __ffma2_rn(mr3, __ffma2_rn(a3, dx, wx), p[3]);
-    p[4] = __ffma2_rn(mr3, __ffma2_rn(a3, dy, wy), p[4]);
-    p[5] = __ffma2_rn(mr3, __ffma2_rn(a3, dz, wz), p[5]);
   }
 }
 
@@ -355,15 +359,17 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     }
   }
 
-  // packed loop: the i-particle in both lanes, negated
-  constexpr bool kPk = NB_MIXED_PACKED && IPT == 1;
-  float2 nxh[3], nxl[3], nv[3];
+  // packed loop: each i-particle in both lanes, negated
+  constexpr bool kPk = NB_MIXED_PACKED && IPT <= 2;
+  float2 nxh[IPT][3], nxl[IPT][3], nv[IPT][3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    nxh[c] = make_float2(-xh[0][c], -xh[0][c]);
-    nxl[c] = make_float2(-xl[0][c], -xl[0][c]);
-    nv[c] = make_float2(-vi[0][c], -vi[0][c]);
-  }
+  for (int k = 0; k < IPT; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      nxh[k][c] = make_float2(-xh[k][c], -xh[k][c]);
+      nxl[k][c] = make_float2(-xl[k][c], -xl[k][c]);
+      nv[k][c] = make_float2(-vi[k][c], -vi[k][c]);
+    }
 
   const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
   if (ntiles > 0) {
@@ -439,17 +445,21 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     if constexpr (kPk) {
       const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
       const float2 e2 = make_float2(eps2, eps2);
-      float2 p2[7];
+      float2 p2[IPT][7];
 #pragma unroll
-      for (int c = 0; c < 7; ++c) p2[c] = make_float2(0.0f, 0.0f);
+      for (int k = 0; k < IPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) p2[k][c] = make_float2(0.0f, 0.0f);
       if (__any_sync(0xffffffffu, hit))
-        mixed_pair_pass<JT, kSelf>(pt, nxh, nxl, nv, rel[0], e2, p2);
+        mixed_pair_pass<IPT, JT, kSelf>(pt, nxh, nxl, nv, rel, e2, p2);
       else if (__all_sync(0xffffffffu, far))
-        mixed_pair_pass<JT, kFar>(pt, nxh, nxl, nv, rel[0], e2, p2);
+        mixed_pair_pass<IPT, JT, kFar>(pt, nxh, nxl, nv, rel, e2, p2);
       else
-        mixed_pair_pass<JT, kNear>(pt, nxh, nxl, nv, rel[0], e2, p2);
+        mixed_pair_pass<IPT, JT, kNear>(pt, nxh, nxl, nv, rel, e2, p2);
 #pragma unroll
-      for (int c = 0; c < 7; ++c) p[0][c] = p2[c].x + p2[c].y;
+      for (int k = 0; k < IPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) p[k][c] = p2[k][c].x + p2[k][c].y;
     } else {
       if (__any_sync(0xffffffffu, hit))
         mixed_tile_pass<IPT, JT, kSelf>(sm.A[buf], sm.B[buf], sm.C[buf], xh, xl, vi, rel, eps2, p);
