@@ -188,7 +188,8 @@ int get_rows(nb_ctx* c, const double* src, int rows, int64_t first, int64_t coun
 // after sort_interval block steps; the next prediction writes that order
 // (mixed path only: the FP64 path has no far-tile pass to gain from it)
 int ensure_sorted(nb_ctx* c) {
-  if (c->n_clusters > 0 || c->n <= 0 || c->precision != NB_MIXED) return NB_OK;
+  if (c->n_clusters > 0) return nb_ensemble_ensure_sorted(c);  // within each cluster
+  if (c->n <= 0 || c->precision != NB_MIXED) return NB_OK;
   if (c->perm_valid && c->perm_age < c->sort_interval) return NB_OK;
   NB_CUDA(c, nb_spatial_sort(c));
   c->perm_valid = true;

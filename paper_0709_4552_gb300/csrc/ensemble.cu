@@ -15,6 +15,7 @@
 //
 // Cluster c owns particles [off[c], off[c+1]) of the j-store and the same
 // slots of the active list and of the force results.
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -73,6 +74,13 @@ struct Batch {
   int64_t* ctrl = nullptr;         // [4]: any active, iterations, interactions (as int64), spare
   BParams* prm = nullptr;
   double* esum = nullptr;          // [2C] per-cluster energies
+  // spatial order within each cluster (mixed ensembles of at most 2^11 clusters)
+  int64_t* tile_off = nullptr;     // [C+1] first 128-row box tile of each cluster
+  int32_t* tile_cl = nullptr;      // [ntiles] cluster of each box tile
+  float4* tbox = nullptr;          // [2 ntiles] boxes of the predicted tiles
+  double* cbox = nullptr;          // [6C] bounding box of each cluster
+  int64_t ntiles = 0;
+  int cl_bits = 0;                 // bits of a cluster number in the sort keys
   // host
   std::vector<int64_t> h_off;
   int nt = 128;                    // i-tile (threads per CTA) of the force items: 32 or 128
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(NT, mixed_min_ctas(NT)) b_force_mixed(
     const int32_t* __restrict__ nsplit, const int64_t* __restrict__ jps, const int64_t* __restrict__ item_off,
     const int64_t* __restrict__ part_off, const int64_t* __restrict__ pstride, double* __restrict__ F,
     int64_t fstride, double* __restrict__ part, const float4* __restrict__ tbox,
-    unsigned long long* __restrict__ wq) {
+    const int64_t* __restrict__ tile_off, unsigned long long* __restrict__ wq) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   __shared__ int64_t s_item;
   const int64_t total = item_off[C];
@@ -444,8 +452,11 @@ __global__ void __launch_bounds__(NT, mixed_min_ctas(NT)) b_force_mixed(
     const int64_t jhi = min(jlo + jps[c], off[c + 1]);
     const bool fin = nsplit[c] == 1;
     double* out = fin ? F + off[c] : part + part_off[c] + split * 7 * pstride[c];
+    // boxes: of the whole j-store (one system) or of the cluster's own tiles
+    const float4* tb = tbox ? (tile_off ? tbox + 2 * tile_off[c] : tbox) : nullptr;
     nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_pad, act + off[c], nact[c], itile * (NT * IPT),
-                                 eps2f[c], out, fin ? fstride : pstride[c], fin, tbox);
+                                 eps2f[c], out, fin ? fstride : pstride[c], fin, tb, nullptr,
+                                 tile_off ? off[c] : 0);
   }
 }
 
@@ -513,6 +524,91 @@ __global__ void b_reduce(int32_t C, const int64_t* __restrict__ off, const int32
     }
     if (ty == 0 && k < n) F[r * fstride + o + k] = r == 6 ? -sm[0][tx] : sm[0][tx];
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spatial order within each cluster: cluster boxes, keys = cluster number
+// above a 21-bit Morton code of the position in the cluster's box (a stable
+// sort keeps every cluster on its own rows), boxes of 128-row tiles counted
+// from each cluster's first row
+// ---------------------------------------------------------------------------
+__global__ void b_cluster_bbox(const int64_t* __restrict__ off, int64_t n_pad, const double* __restrict__ x,
+                               double* __restrict__ cbox) {
+  const int c = blockIdx.x;
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int64_t s = off[c] + threadIdx.x; s < off[c + 1]; s += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      const double v = x[d * n_pad + s];
+      lo[d] = fmin(lo[d], v);
+      hi[d] = fmax(hi[d], v);
+    }
+  __shared__ double sm[6][256];
+  for (int d = 0; d < 3; ++d) {
+    sm[d][threadIdx.x] = lo[d];
+    sm[3 + d][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int d = 0; d < 3; ++d) {
+        sm[d][threadIdx.x] = fmin(sm[d][threadIdx.x], sm[d][threadIdx.x + w]);
+        sm[3 + d][threadIdx.x] = fmax(sm[3 + d][threadIdx.x], sm[3 + d][threadIdx.x + w]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) cbox[6 * c + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void b_cluster_keys(int64_t N, int64_t n_pad, const int32_t* __restrict__ cid,
+                               const double* __restrict__ x, const double* __restrict__ cbox,
+                               uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cid[s];
+    const double* bx = cbox + 6 * c;
+    double scale = fmax(bx[3] - bx[0], fmax(bx[4] - bx[1], bx[5] - bx[2]));
+    scale = scale > 0.0 ? 127.0 / scale : 0.0;
+    uint32_t q[3];
+    for (int d = 0; d < 3; ++d) {
+      double f = (x[d * n_pad + s] - bx[d]) * scale;
+      f = f < 0.0 ? 0.0 : (f > 127.0 ? 127.0 : f);
+      q[d] = (uint32_t)f;
+    }
+    key[s] = ((uint32_t)c << 21) | nb_spread10(q[0]) | (nb_spread10(q[1]) << 1) | (nb_spread10(q[2]) << 2);
+    val[s] = (int32_t)s;
+  }
+}
+
+// one warp per box tile: box of the predicted FP32 hi positions, (lo, rmax), (hi, 0)
+__global__ void b_tile_boxes(int64_t ntiles, const int32_t* __restrict__ tile_cl,
+                             const int64_t* __restrict__ tile_off, const int64_t* __restrict__ off,
+                             const float4* __restrict__ jA, float4* __restrict__ box) {
+  const int64_t g = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= ntiles) return;
+  const int c = tile_cl[g];
+  const int64_t s0 = off[c] + (g - tile_off[c]) * NB_BOX_TILE;
+  const int64_t s1 = min(s0 + NB_BOX_TILE, off[c + 1]);
+  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX}, r = 0.0f;
+  for (int64_t s = s0 + lane; s < s1; s += 32) {
+    const float4 a = jA[s];
+    const float p[3] = {a.x, a.y, a.z};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], p[d]);
+      hi[d] = fmaxf(hi[d], p[d]);
+      r = fmaxf(r, fabsf(p[d]));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+    r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+  }
+  if (lane == 0) {
+    box[2 * g] = make_float4(lo[0], lo[1], lo[2], r);
+    box[2 * g + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
   }
 }
 
@@ -663,7 +759,7 @@ void batch_free(Batch* b) {
   if (!b) return;
   void* p[] = {b->off, b->eps2f, b->eps2d, b->cid, b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min,
                b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->ritem_off, b->part_off,
-               b->pstride, b->ctrl, b->prm, b->esum, b->wq};
+               b->pstride, b->ctrl, b->prm, b->esum, b->wq, b->tile_off, b->tile_cl, b->tbox, b->cbox};
   for (void* q : p)
     if (q) cudaFree(q);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -715,6 +811,19 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   BA(b->ch_lo, b->nchunks) BA(b->ch_hi, b->nchunks) BA(b->cl_ch0, C + 1) BA(b->ch_min, b->nchunks)
   BA(b->ch_cnt, b->nchunks) BA(b->tnext, C) BA(b->nact, C) BA(b->itiles, C) BA(b->nsplit, C) BA(b->jps, C)
   BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->wq, 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
+  // box tiles of 128 rows counted from each cluster's first row
+  std::vector<int64_t> toff(C + 1);
+  std::vector<int32_t> tcl;
+  for (int32_t q = 0; q < C; ++q) {
+    toff[q] = (int64_t)tcl.size();
+    for (int64_t s = h_off[q]; s < h_off[q + 1]; s += NB_BOX_TILE) tcl.push_back(q);
+  }
+  toff[C] = (int64_t)tcl.size();
+  b->ntiles = toff[C];
+  while (b->cl_bits < 31 && ((int64_t)1 << b->cl_bits) < C) ++b->cl_bits;
+  if (C > 1 && b->cl_bits <= 11) {
+    BA(b->tile_off, C + 1) BA(b->tile_cl, b->ntiles) BA(b->tbox, 2 * b->ntiles) BA(b->cbox, 6 * C)
+  }
 #undef BA
   auto H2D = [&](void* d, const void* h, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream);
@@ -726,6 +835,10 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   H2D(b->ch_lo, chlo.data(), chlo.size() * sizeof(int64_t));
   H2D(b->ch_hi, chhi.data(), chhi.size() * sizeof(int64_t));
   H2D(b->cl_ch0, clch0.data(), clch0.size() * sizeof(int32_t));
+  if (b->tile_off) {
+    H2D(b->tile_off, toff.data(), toff.size() * sizeof(int64_t));
+    H2D(b->tile_cl, tcl.data(), tcl.size() * sizeof(int32_t));
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream);
   if (e == cudaSuccess && b->N > 0) {
     fill_cid<<<grid_for(b->N, 256, 4096), 256, 0, c->stream>>>(b->N, b->off, C, b->cid);
@@ -785,13 +898,19 @@ bool single_boxes(const nb_ctx* c, const Batch* b) {
   return c->precision == NB_MIXED && c->n_clusters == 0 && b->C == 1;
 }
 
+// an ensemble of mixed clusters kept in spatial order within each cluster
+bool cluster_boxes(const nb_ctx* c, const Batch* b) {
+  return c->precision == NB_MIXED && c->n_clusters > 0 && b->tile_off != nullptr;
+}
+
 template <int NT>
 void launch_force(nb_ctx* c, Batch* b, bool mixed) {
   if (mixed)
     b_force_mixed<NT, kMixIPT, kMixJT><<<b->grid_mixed, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
-        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part, single_boxes(c, b) ? c->tbox : nullptr,
-        b->wq);
+        b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part,
+        single_boxes(c, b) ? c->tbox : (cluster_boxes(c, b) ? b->tbox : nullptr),
+        cluster_boxes(c, b) ? b->tile_off : nullptr, b->wq);
   else
     b_force_fp64<NT, kF64JT><<<b->grid_fp64, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2d, c->n_pad, c->xp, c->vp, c->m, c->act, b->nact, b->itiles, b->nsplit, b->jps,
@@ -806,6 +925,10 @@ cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
   if (single_boxes(c, b)) {
     cudaError_t e = nb_launch_tile_boxes(c);  // boxes of the predicted tiles for the far test
     if (e != cudaSuccess) return e;
+  } else if (cluster_boxes(c, b)) {
+    b_tile_boxes<<<(unsigned)((b->ntiles + 7) / 8), 256, 0, c->stream>>>(b->ntiles, b->tile_cl, b->tile_off, b->off,
+                                                                        c->jA, b->tbox);
+    c->launches += 1;
   }
   if (b->nt == 32)
     launch_force<32>(c, b, mixed);
@@ -1005,6 +1128,25 @@ int nb_integrate_graph(nb_ctx* c, double t_end) {
   return run_graph(c, b, t_end);
 }
 
+int nb_ensemble_ensure_sorted(nb_ctx* c) {
+  Batch* b = batch_of(c);
+  if (!b || !cluster_boxes(c, b) || b->N <= 0) return NB_OK;
+  // once per set of particles: a cluster moves little against its own size in
+  // the time units an ensemble run covers, and a renewal would cost the graph
+  // loop a host round trip per segment
+  if (c->perm_valid) return NB_OK;
+  b_cluster_bbox<<<b->C, 256, 0, c->stream>>>(b->off, c->n_pad, c->x, b->cbox);
+  b_cluster_keys<<<grid_for(b->N, 256, c->sm_count * 16), 256, 0, c->stream>>>(b->N, c->n_pad, b->cid, c->x, b->cbox,
+                                                                              c->skey[0], c->sval[0]);
+  c->launches += 2;
+  if (cudaGetLastError() != cudaSuccess || nb_order_rows_by_keys(c, 21 + b->cl_bits) != cudaSuccess) return NB_ECUDA;
+  c->perm_valid = true;
+  c->perm_age = 0;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}
+
 extern "C" {
 
 int nb_ensemble_create(nb_ctx** out, int32_t n_clusters, const int64_t* offsets, const double* eps, int precision,
@@ -1040,6 +1182,8 @@ int nb_ensemble_initial_forces_and_dt(nb_ctx* c) {
   if (!c || !c->ens) return NB_EINVAL;
   Batch* b = batch_of(c);
   if (c->n < b->N) return NB_ESTATE;
+  const int rs = nb_ensemble_ensure_sorted(c);
+  if (rs != NB_OK) return rs;
   if (set_params(c, b, 0.0) != cudaSuccess) return NB_ECUDA;
   if (all_forces(c, b) != cudaSuccess) return NB_ECUDA;
   b_initial_dt<<<grid_for(b->N, 256, c->sm_count * 16), 256, 0, c->stream>>>(b->N, c->n_pad, c->F, c->n_pad, b->prm,

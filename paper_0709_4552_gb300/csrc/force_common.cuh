@@ -282,12 +282,12 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
                                            const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                            float eps2, double* __restrict__ out, int64_t ostride,
                                            bool finalize, const float4* __restrict__ tbox = nullptr,
-                                           const int32_t* __restrict__ ord = nullptr) {
+                                           const int32_t* __restrict__ ord = nullptr, int64_t box_origin = 0) {
   // list: j-store slots of the i-particles.  ord (optional): the list
   // positions in processing order (a caller's list visited in spatial
-  // order); results always go to the list positions.  tbox (optional,
-  // j-ranges aligned to JT slots): boxes of every NB_BOX_TILE slots up to
-  // the padded end of the j-store, which allow the far-tile pass.
+  // order); results always go to the list positions.  tbox (optional):
+  // boxes of every NB_BOX_TILE slots from slot box_origin on (j-ranges start
+  // at box_origin plus a multiple of JT), which allow the far-tile pass.
   const int tid = threadIdx.x;
   float xh[IPT][3], xl[IPT][3], vi[IPT][3];
   int64_t self[IPT];
@@ -433,7 +433,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
       far = true;
 #pragma unroll
       for (int b = 0; b < kBoxes; ++b) {
-        const int64_t t = jt / NB_BOX_TILE + b;
+        const int64_t t = (jt - box_origin) / NB_BOX_TILE + b;
         const float4 blo = tbox[2 * t], bhi = tbox[2 * t + 1];
         const float gx = fmaxf(0.0f, fmaxf(blo.x - whi[0], wlo[0] - bhi.x));
         const float gy = fmaxf(0.0f, fmaxf(blo.y - whi[1], wlo[1] - bhi.y));

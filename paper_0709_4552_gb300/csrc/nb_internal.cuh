@@ -163,6 +163,8 @@ cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
 
 // spatial.cu
 cudaError_t nb_spatial_sort(nb_ctx* c);       // new resident order from the current positions
+// new resident order: rows stably sorted by skey[0] (low `bits` bits), sval[0] = row numbers
+cudaError_t nb_order_rows_by_keys(nb_ctx* c, int bits);
 cudaError_t nb_unsort(nb_ctx* c);             // back to particle order (perm_valid = false)
 // caller list of particles -> list of slots in c->mlist (*out = d_list when unsorted)
 cudaError_t nb_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out);
@@ -179,9 +181,21 @@ int nb_ensure_sorted(nb_ctx* c);
 
 // ensemble.cu
 void nb_ensemble_free(nb_ctx* c);
+// (re)compute the spatial order within each cluster when it is due (mixed ensembles)
+int nb_ensemble_ensure_sorted(nb_ctx* c);
 int nb_integrate_graph(nb_ctx* c, double t_end);
 
 // ---- device helpers ---------------------------------------------------------
+// the low 10 bits of a moved to every third bit (one axis of a Morton code)
+__device__ __forceinline__ uint32_t nb_spread10(uint32_t a) {
+  a &= 0x3FFu;
+  a = (a | (a << 16)) & 0x030000FFu;
+  a = (a | (a << 8)) & 0x0300F00Fu;
+  a = (a | (a << 4)) & 0x030C30C3u;
+  a = (a | (a << 2)) & 0x09249249u;
+  return a;
+}
+
 __device__ __forceinline__ float nb_rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -77,15 +77,6 @@ __global__ void bbox_final(int nb, const double* __restrict__ red, double* __res
   if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
-__device__ __forceinline__ uint32_t spread10(uint32_t a) {  // 10 bits -> every third bit
-  a &= 0x3FFu;
-  a = (a | (a << 16)) & 0x030000FFu;
-  a = (a | (a << 8)) & 0x0300F00Fu;
-  a = (a | (a << 4)) & 0x030C30C3u;
-  a = (a | (a << 2)) & 0x09249249u;
-  return a;
-}
-
 __global__ void morton_keys(int64_t N, int64_t n_pad, const double* __restrict__ x, const double* __restrict__ box,
                             uint32_t* __restrict__ key, int32_t* __restrict__ val) {
   double scale = fmax(box[3] - box[0], fmax(box[4] - box[1], box[5] - box[2]));
@@ -97,7 +88,7 @@ __global__ void morton_keys(int64_t N, int64_t n_pad, const double* __restrict__
       f = f < 0.0 ? 0.0 : (f > 1023.0 ? 1023.0 : f);
       q[c] = (uint32_t)f;
     }
-    key[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+    key[i] = nb_spread10(q[0]) | (nb_spread10(q[1]) << 1) | (nb_spread10(q[2]) << 2);
     val[i] = (int32_t)i;
   }
 }
@@ -327,17 +318,12 @@ cudaError_t sort_pairs(nb_ctx* c, int64_t n, int bits, int* cur) {
 
 }  // namespace
 
-cudaError_t nb_spatial_sort(nb_ctx* c) {
+// stable sort of the rows by the keys in skey[0] (values = row numbers in
+// sval[0]) on the low `bits` bits, then the state reordered to that order
+cudaError_t nb_order_rows_by_keys(nb_ctx* c, int bits) {
   const int64_t N = c->n;
-  if (N <= 0) return cudaSuccess;
-  const int nbb = grid_for(N, kSortThreads, 1024);
-  double* box = c->red + NB_BBOX_OFFSET;
-  bbox_partial<<<nbb, kSortThreads, 0, c->stream>>>(N, c->n_pad, c->x, c->red);
-  bbox_final<<<1, kSortThreads, 0, c->stream>>>(nbb, c->red, box);
-  morton_keys<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->n_pad, c->x, box, c->skey[0],
-                                                                         c->sval[0]);
   int cur = 0;
-  cudaError_t e = sort_pairs(c, N, 30, &cur);
+  cudaError_t e = sort_pairs(c, N, bits, &cur);
   if (e != cudaSuccess) return e;
   // sval[cur][s] = the current row that becomes row s
   const int32_t* sigma = c->sval[cur];
@@ -349,8 +335,23 @@ cudaError_t nb_spatial_sort(nb_ctx* c) {
   e = cudaMemcpyAsync(c->perm, np, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return e;
   invert_perm<<<g, 256, 0, c->stream>>>(N, c->perm, c->iperm);
-  c->launches += 5;
+  c->launches += 2;
   return cudaGetLastError();
+}
+
+cudaError_t nb_spatial_sort(nb_ctx* c) {
+  const int64_t N = c->n;
+  if (N <= 0) return cudaSuccess;
+  const int nbb = grid_for(N, kSortThreads, 1024);
+  double* box = c->red + NB_BBOX_OFFSET;
+  bbox_partial<<<nbb, kSortThreads, 0, c->stream>>>(N, c->n_pad, c->x, c->red);
+  bbox_final<<<1, kSortThreads, 0, c->stream>>>(nbb, c->red, box);
+  morton_keys<<<grid_for(N, 256, c->sm_count * 16), 256, 0, c->stream>>>(N, c->n_pad, c->x, box, c->skey[0],
+                                                                         c->sval[0]);
+  c->launches += 3;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return nb_order_rows_by_keys(c, 30);
 }
 
 cudaError_t nb_unsort(nb_ctx* c) {

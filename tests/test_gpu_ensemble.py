@@ -69,18 +69,24 @@ def _ens(nb, prec, off, m, x, v, eps, t_end):
     return e
 
 
-def test_ensemble_initial_forces_are_per_cluster(nbl):
-    sizes = [100, 37, 512, 256, 1]
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ensemble_initial_forces_are_per_cluster(nbl, prec):
+    # the mixed ensemble keeps each cluster in spatial order on its own rows;
+    # particle indices at the ABI are unchanged
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    sizes = [100, 37, 512, 256, 1, 3000, 129]
     off, m, x, v, eps = _ensemble_ics(sizes, 500)
-    with _ens(nbl, nbl.NB_FP64, off, m, x, v, eps, 2.0 ** -6) as e:
+    with _ens(nbl, P, off, m, x, v, eps, 2.0 ** -6) as e:
         st = e.get_particles(0, int(off[-1]))
+    assert np.array_equal(st["x"], x) and np.array_equal(st["m"], m)
     for q in range(len(sizes)):
         a, b = off[q], off[q + 1]
         ar, jr, pr = oracle.forces(m[a:b], x[a:b], v[a:b], eps[q], compensated=True)
         if b - a > 1:
-            assert rel_vec(st["a"][a:b], ar).max() < 1e-12
-            assert rel_vec(st["jerk"][a:b], jr).max() < 1e-12
-            assert rel_scalar(st["pot"][a:b], pr).max() < 1e-12
+            assert rel_vec(st["a"][a:b], ar).max() < tol
+            assert rel_vec(st["jerk"][a:b], jr).max() < tol
+            assert rel_scalar(st["pot"][a:b], pr).max() < tol
         else:
             assert np.all(st["a"][a:b] == 0.0) and np.all(st["pot"][a:b] == 0.0)
 
