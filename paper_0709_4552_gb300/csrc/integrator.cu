@@ -183,24 +183,6 @@ __global__ void initial_dt_kernel(int64_t N, int64_t n_pad, const double* __rest
   }
 }
 
-// store force results of list positions into the master a/jk/pot arrays
-__global__ void store_forces_kernel(int64_t n, int64_t n_pad, const int32_t* __restrict__ list,
-                                    const double* __restrict__ F, int64_t fstride,
-                                    double* __restrict__ a, double* __restrict__ jk,
-                                    double* __restrict__ pot) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = list[k];
-    i = i < 0 ? 0 : (i >= n_pad ? n_pad - 1 : i);  // never out of bounds on a bad list
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      a[c * n_pad + i] = F[c * fstride + k];
-      jk[c * n_pad + i] = F[(3 + c) * fstride + k];
-    }
-    pot[i] = F[6 * fstride + k];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Block selection (Sec. 4.1 step 2): t_next = min_i (t_i + dt_i); active
 // list = ascending {i : t_i + dt_i == t_next}.  Positive doubles order like
@@ -466,14 +448,6 @@ cudaError_t nb_launch_initial_dt(nb_ctx* c) {
   initial_dt_kernel<<<grid_for(c->n, kThreads, c->sm_count * 16), kThreads, 0, c->stream>>>(
       c->n, c->n_pad, c->F, c->n_pad, c->eta, c->dt_min, c->dt_max, c->a, c->jk, c->pot, c->t, c->dt,
       c->status);
-  return cudaGetLastError();
-}
-
-cudaError_t nb_launch_store_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
-  if (n <= 0) return cudaSuccess;
-  c->launches += 1;
-  store_forces_kernel<<<grid_for(n, kThreads, c->sm_count * 16), kThreads, 0, c->stream>>>(
-      n, c->n_pad, d_list, c->F, c->n_pad, c->a, c->jk, c->pot);
   return cudaGetLastError();
 }
 

@@ -134,7 +134,6 @@ cudaError_t nb_launch_predict(nb_ctx* c, double t, bool own_time);
 cudaError_t nb_launch_select(nb_ctx* c);    // writes act, sel_cnt[total], sel_min[result]
 cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t);
 cudaError_t nb_launch_initial_dt(nb_ctx* c);
-cudaError_t nb_launch_store_forces(nb_ctx* c, const int32_t* d_list, int64_t n);
 cudaError_t nb_launch_energy(nb_ctx* c, const double* d_pot, double* d_out2);
 cudaError_t nb_launch_fill_ident(nb_ctx* c);
 cudaError_t nb_launch_aos_to_soa(const double* src, double* dst, int64_t count, int64_t stride_dst,
