@@ -629,7 +629,7 @@ def main():
                                   "sample": f"{k} active x N={N}", "vs_mixed": fp64_rate / value * ws,
                                   "fp64_pipe_frac": fp64_rate * 32 / (pk["fp64_tflops"] * 1e12 / 2)}
         extra["peaks_measured"] = pk
-        if not args.no_cpu:
+        if not args.no_cpu and ws == 1:  # the host baseline is taken at N = 1 only
             import oracle
             oracle.build()
             t0 = time.perf_counter()
