@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5", "tapp", "c3sweep"],
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c2", "c4", "c5", "tapp", "c3sweep", "c4init"],
                     help="c3 (default): the timed benchmark; c2/c4/c5: long integrations; tapp: time per "
                          "N-body time unit vs N and the per-task model; one JSON line each")
     ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
@@ -291,6 +292,34 @@ def run_integration(args):
         if w == "c5":
             out["wall_per_nbody_time_unit_s_extrapolated"] = wall / t_end
         print(json.dumps(out), flush=True)
+        return
+
+    if w == "c4init":
+        # configuration 4's clusters, all particles at once (the persistent force kernel on one
+        # full force evaluation per cluster, launched outside the graph): a short case for
+        # profiling the batched kernel
+        sizes = inputs.ensemble_sizes(512, 256, 16384, seed=7)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        eps = 1.0 / (4.0 * sizes.astype(np.float64) ** (1.0 / 3.0))
+        parts = [inputs.plummer(int(n), 10000 + q, "salpeter") for q, n in enumerate(sizes)]
+        m = np.concatenate([p[0] for p in parts])
+        x = np.concatenate([p[1] for p in parts])
+        v = np.concatenate([p[2] for p in parts])
+        e = nb.Ensemble(off, eps, nb.NB_MIXED, 0)
+        e.set_params(0.01, 0.01, 2.0 ** -22, 1.0 / 16)
+        e.set_j_particles(0, m, x, v)
+        walls = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e.initial_forces_and_dt()
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+        inter = float((sizes.astype(np.float64) ** 2).sum())
+        e.close()
+        print(json.dumps({"workload": "c4init", "clusters": 512, "N_total": int(off[-1]),
+                          "interactions": inter, "wall_s": walls,
+                          "interactions_per_s": inter / min(walls[1:])}), flush=True)
         return
 
     if w == "c4":
