@@ -31,6 +31,7 @@ namespace {
 #define NB_ENS_ITEM_WAVES 4
 #endif
 constexpr int kItemWaves = NB_ENS_ITEM_WAVES;  // force items planned per resident CTA
+constexpr int kCorrItem = 128;    // active particles per corrector item (= its threads per CTA)
 constexpr int kSelChunk = 512;    // particles per selection chunk (chunks never straddle clusters)
 // batched item shapes: i-tile = threads per CTA, one i per thread.  An
 // ensemble of small clusters has small active blocks (n = 0.20 N^0.81 is 18
@@ -68,6 +69,7 @@ struct Batch {
   int64_t* jps = nullptr;          // [C] j per split
   int64_t* item_off = nullptr;     // [C+1]
   int64_t* ritem_off = nullptr;    // [C+1] split-reduction items (32 positions) per cluster
+  int64_t* citem_off = nullptr;    // [C+1] corrector items (kCorrItem active particles) per cluster
   unsigned long long* wq = nullptr;  // force-item counter of the current step
   int64_t* part_off = nullptr;     // [C]
   int64_t* pstride = nullptr;      // [C]
@@ -252,7 +254,8 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
                        int32_t* __restrict__ itiles, int32_t* __restrict__ nsplit, int64_t* __restrict__ jps,
                        int64_t* __restrict__ item_off, int64_t* __restrict__ part_off,
                        int64_t* __restrict__ pstride, int64_t* __restrict__ ritem_off,
-                       unsigned long long* __restrict__ wq, int64_t* __restrict__ ctrl,
+                       int64_t* __restrict__ citem_off, unsigned long long* __restrict__ wq,
+                       int64_t* __restrict__ ctrl,
                        const BParams* __restrict__ prm, nb_dev_status* __restrict__ st,
                        cudaGraphConditionalHandle handle, int use_handle) {
   __shared__ int64_t sh[1024];
@@ -281,10 +284,10 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
   __syncthreads();
   for (int attempt = 0; attempt < 40; ++attempt) {
     const int64_t L = s_L;
-    int64_t item_carry = 0, part_carry = 0, ritem_carry = 0;
+    int64_t item_carry = 0, part_carry = 0, ritem_carry = 0, citem_carry = 0;
     for (int c0 = 0; c0 < C; c0 += blockDim.x) {
       const int c = c0 + t;
-      int64_t items = 0, psz = 0, ritems = 0;
+      int64_t items = 0, psz = 0, ritems = 0, citems = 0;
       int32_t it = 0, ns = 1;
       int64_t jp = 0, ps = 0;
       if (c < C) {
@@ -303,11 +306,13 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
         items = (int64_t)it * s;
         psz = s > 1 ? 7 * s * ps : 0;
         ritems = s > 1 ? 7 * ((n + 31) / 32) : 0;
+        citems = (n + kCorrItem - 1) / kCorrItem;
       }
-      int64_t tot_items, tot_part, tot_ritems;
+      int64_t tot_items, tot_part, tot_ritems, tot_citems;
       const int64_t ex_items = block_excl_scan(items, sh, &tot_items);
       const int64_t ex_part = block_excl_scan(psz, sh, &tot_part);
       const int64_t ex_ritems = block_excl_scan(ritems, sh, &tot_ritems);
+      const int64_t ex_citems = block_excl_scan(citems, sh, &tot_citems);
       if (c < C) {
         itiles[c] = it;
         nsplit[c] = ns;
@@ -316,14 +321,17 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
         item_off[c] = item_carry + ex_items;
         part_off[c] = part_carry + ex_part;
         ritem_off[c] = ritem_carry + ex_ritems;
+        citem_off[c] = citem_carry + ex_citems;
       }
       item_carry += tot_items;
       part_carry += tot_part;
       ritem_carry += tot_ritems;
+      citem_carry += tot_citems;
     }
     if (t == 0) {
       item_off[C] = item_carry;
       ritem_off[C] = ritem_carry;
+      citem_off[C] = citem_carry;
       s_retry = part_carry > part_cap;
       if (s_retry) s_L = s_L * 2;
     }
@@ -349,6 +357,7 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
       go = 0;
       item_off[C] = 0;
       ritem_off[C] = 0;
+      citem_off[C] = 0;
     }
     ctrl[0] = go;
     if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
@@ -621,7 +630,7 @@ __device__ __forceinline__ double pow2_floor_b(double x) {
 }
 
 // corrector + block-step rule (Sec. 4.1 step 5), per slot of active clusters
-__global__ void b_correct(int64_t N, int64_t n_pad, const int32_t* __restrict__ cid,
+__global__ void b_correct(int32_t C, int64_t n_pad, const int64_t* __restrict__ citem_off,
                           const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
                           const double* __restrict__ tnext, const int32_t* __restrict__ act,
                           const double* __restrict__ F, int64_t fstride, const BParams* __restrict__ prm,
@@ -630,9 +639,13 @@ __global__ void b_correct(int64_t N, int64_t n_pad, const int32_t* __restrict__ 
                           double* __restrict__ dt, const double* __restrict__ xp,
                           const double* __restrict__ vp, nb_dev_status* __restrict__ st) {
   const double eta = prm->eta, dt_min = prm->dt_min, dt_max = prm->dt_max;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-    const int c = cid[s];
-    if (s - off[c] >= nact[c]) continue;
+  // items of kCorrItem active particles of one cluster (planned by b_plan)
+  const int64_t total = citem_off[C];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_cluster(citem_off, C, item);
+    const int64_t k = (item - citem_off[c]) * kCorrItem + threadIdx.x;
+    if (k >= nact[c]) continue;
+    const int64_t s = off[c] + k;
     int64_t i = act[s];
     i = i < 0 ? 0 : (i >= n_pad ? n_pad - 1 : i);
     const double t = tnext[c];
@@ -758,7 +771,7 @@ int grid_for(int64_t n, int threads, int cap) {
 void batch_free(Batch* b) {
   if (!b) return;
   void* p[] = {b->off, b->eps2f, b->eps2d, b->cid, b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min,
-               b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->ritem_off, b->part_off,
+               b->ch_cnt, b->tnext, b->nact, b->itiles, b->nsplit, b->jps, b->item_off, b->ritem_off, b->citem_off, b->part_off,
                b->pstride, b->ctrl, b->prm, b->esum, b->wq, b->tile_off, b->tile_cl, b->tbox, b->cbox};
   for (void* q : p)
     if (q) cudaFree(q);
@@ -810,7 +823,7 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
   BA(b->off, C + 1) BA(b->eps2f, C) BA(b->eps2d, C) BA(b->cid, c->n_pad) BA(b->ch_cluster, b->nchunks)
   BA(b->ch_lo, b->nchunks) BA(b->ch_hi, b->nchunks) BA(b->cl_ch0, C + 1) BA(b->ch_min, b->nchunks)
   BA(b->ch_cnt, b->nchunks) BA(b->tnext, C) BA(b->nact, C) BA(b->itiles, C) BA(b->nsplit, C) BA(b->jps, C)
-  BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->wq, 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
+  BA(b->item_off, C + 1) BA(b->ritem_off, C + 1) BA(b->citem_off, C + 1) BA(b->wq, 1) BA(b->part_off, C) BA(b->pstride, C) BA(b->ctrl, 4) BA(b->prm, 1) BA(b->esum, 2 * C)
   // box tiles of 128 rows counted from each cluster's first row
   std::vector<int64_t> toff(C + 1);
   std::vector<int32_t> tcl;
@@ -887,7 +900,7 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
-                                    b->ritem_off, b->wq, b->ctrl,
+                                    b->ritem_off, b->citem_off, b->wq, b->ctrl,
                                     b->prm, c->status, 0, 0);
   return cudaGetLastError();
 }
@@ -953,14 +966,14 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
-                                    b->ritem_off, b->wq, b->ctrl,
+                                    b->ritem_off, b->citem_off, b->wq, b->ctrl,
                                     b->prm, c->status, handle, use_handle);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = body_after_plan(c, b, false)) != cudaSuccess) return e;
-  const int g = grid_for(b->N, 128, c->sm_count * 32);
-  b_correct<<<g, 128, 0, c->stream>>>(b->N, c->n_pad, b->cid, b->off, b->nact, b->tnext, c->act, c->F, c->n_pad,
-                                      b->prm, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->status);
+  b_correct<<<c->sm_count * 16, kCorrItem, 0, c->stream>>>(b->C, c->n_pad, b->citem_off, b->off, b->nact, b->tnext,
+                                                           c->act, c->F, c->n_pad, b->prm, c->x, c->v, c->a, c->jk,
+                                                           c->pot, c->t, c->dt, c->xp, c->vp, c->status);
   c->launches += 5;
   return cudaGetLastError();
 }
