@@ -501,6 +501,23 @@ def run_integration(args):
             wall_g = time.perf_counter() - t0
             kg, wg = g.energy()
             g.close()
+            # ... and as one persistent cooperative kernel (systems up to 65536)
+            wall_p, drift_p, steps_p = None, None, None
+            if N <= nb.NB_PERSISTENT_MAX_N:
+                q = nb.NBody(N, nb.NB_MIXED, 0)
+                q.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
+                q.set_j_particles(0, m, x, v)
+                q.initial_forces_and_dt()
+                cq0 = q.get_counters()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                q.integrate(1.0, loop=nb.NB_LOOP_PERSISTENT)
+                torch.cuda.synchronize()
+                wall_p = time.perf_counter() - t0
+                steps_p = q.get_counters()["block_steps"] - cq0["block_steps"]
+                kq, wq = q.energy()
+                drift_p = abs((kq + wq) - (k0 + w0)) / abs(k0 + w0)
+                q.close()
             steps = c1["block_steps"] - c0["block_steps"]
             inter = tim["interactions"]
             psteps = inter / N
@@ -512,7 +529,9 @@ def run_integration(args):
                         "model_T_s": tp + tf + tc, "share_force": tf / wall, "share_pred": tp / wall,
                         "share_corr": tc / wall, "share_host_and_select": 1 - (tp + tf + tc) / wall,
                         "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0),
-                        "T_app_graph_s": wall_g, "energy_drift_graph": abs((kg + wg) - (k0 + w0)) / abs(k0 + w0)})
+                        "T_app_graph_s": wall_g, "energy_drift_graph": abs((kg + wg) - (k0 + w0)) / abs(k0 + w0),
+                        "T_app_persistent_s": wall_p, "block_steps_persistent": steps_p,
+                        "energy_drift_persistent": drift_p})
             print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": "mixed",
                           "grape_tau_force_s": 4.3e-10, "rows": out}), flush=True)

@@ -186,11 +186,27 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
 
 /*
  * nb_integrate -- Sec. 4.1 steps 2-6: block steps until every particle has
- * reached t_end (t_end must be a multiple of dt_max).  use_graph != 0 runs
- * the loop as one CUDA graph with a device-side while node (no host round
- * trip per step).  Errors: NB_EINVAL, NB_ENUMERIC, NB_ECUDA.
+ * reached t_end (t_end must be a multiple of dt_max).  loop selects who
+ * drives the steps:
+ *   NB_LOOP_HOST        the host, one launch sequence per block step;
+ *   NB_LOOP_GRAPH       one CUDA graph whose body sits in a device-side while
+ *                       node (no host round trip per step);
+ *   NB_LOOP_PERSISTENT  one cooperative kernel that stays resident for the
+ *                       whole run (one CTA group per SM, three grid barriers
+ *                       per block step, each wait bounded), for systems whose
+ *                       block steps are latency-bound: N <= NB_PERSISTENT_MAX_N.
+ * All three take the same block steps with the same per-particle arithmetic;
+ * sums over j-splits may group differently.  The mixed path renews its
+ * spatial order between launches (graph and persistent loops run segments of
+ * at most the sort interval).  Errors: NB_EINVAL (t_end, loop, N too large
+ * for the persistent loop), NB_ENUMERIC, NB_ETIMEOUT (a bounded device wait
+ * gave up; the state is then undefined), NB_ECUDA.
  */
-int nb_integrate(nb_ctx* ctx, double t_end, int use_graph);
+#define NB_LOOP_HOST        0
+#define NB_LOOP_GRAPH       1
+#define NB_LOOP_PERSISTENT  2
+#define NB_PERSISTENT_MAX_N 65536
+int nb_integrate(nb_ctx* ctx, double t_end, int loop);
 
 /*
  * nb_energy -- kinetic and potential energy of the current state (the paper
@@ -221,6 +237,17 @@ int nb_get_counters(nb_ctx* ctx, int64_t* kernel_launches, int64_t* block_steps)
  * *dt_underflows, may be NULL), bounded wait timeout (NB_ETIMEOUT).
  */
 int nb_check_device_status(nb_ctx* ctx, int64_t* dt_underflows);
+
+/*
+ * nb_check_grid_barrier -- exercises the bounded wait of the persistent
+ * loop's grid barrier on the device: one CTA per SM, three barriers.  With
+ * phantom = 0 every wait completes (NB_OK); with phantom != 0 the barrier
+ * waits for one CTA more than were launched, every CTA gives up after
+ * wait_ms (0 < wait_ms <= 4000) and the call returns NB_ETIMEOUT with the
+ * timeout bit set in the device status (clear it with nb_clear_error); the
+ * context stays usable.  Errors: NB_EINVAL, NB_ENOMEM, NB_ECUDA.
+ */
+int nb_check_grid_barrier(nb_ctx* ctx, int phantom, double wait_ms);
 
 /* nb_last_error / nb_clear_error -- the sticky first error of a context. */
 int nb_last_error(nb_ctx* ctx);

@@ -392,6 +392,7 @@ void nb_destroy(nb_ctx* c) {
   select_device(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   nb_ensemble_free(c);
+  nb_persistent_free(c);
   free_ctx(c);
 }
 
@@ -623,11 +624,15 @@ static int integrate_host_loop(nb_ctx* c, double t_end) {
 int nb_integrate_graph(nb_ctx* c, double t_end);
 extern "C" {
 
-int nb_integrate(nb_ctx* c, double t_end, int use_graph) {
+int nb_integrate(nb_ctx* c, double t_end, int loop) {
   NB_SINGLE(c);
   if (c->n <= 0) return fail(c, NB_ESTATE);
   if (!(t_end > 0.0) || !isfinite(t_end) || fmod(t_end, c->dt_max) != 0.0) return fail(c, NB_EINVAL);
-  int r = use_graph ? nb_integrate_graph(c, t_end) : integrate_host_loop(c, t_end);
+  if (loop != NB_LOOP_HOST && loop != NB_LOOP_GRAPH && loop != NB_LOOP_PERSISTENT) return fail(c, NB_EINVAL);
+  if (loop == NB_LOOP_PERSISTENT && c->n > NB_PERSISTENT_MAX_N) return fail(c, NB_EINVAL);
+  int r = loop == NB_LOOP_GRAPH        ? nb_integrate_graph(c, t_end)
+          : loop == NB_LOOP_PERSISTENT ? nb_integrate_persistent(c, t_end)
+                                       : integrate_host_loop(c, t_end);
   if (r) return r;
   r = device_status_code(c, nullptr);
   if (r == NB_ENUMERIC || r == NB_ETIMEOUT) return fail(c, r);
@@ -677,6 +682,13 @@ int nb_get_counters(nb_ctx* c, int64_t* kernel_launches, int64_t* block_steps) {
 int nb_check_device_status(nb_ctx* c, int64_t* dt_underflows) {
   NB_ENTER(c);
   return device_status_code(c, dt_underflows);
+}
+
+int nb_check_grid_barrier(nb_ctx* c, int phantom, double wait_ms) {
+  NB_ENTER(c);
+  if (!(wait_ms > 0.0) || !(wait_ms <= 4000.0)) return fail(c, NB_EINVAL);
+  const int r = nb_persistent_barrier_check(c, phantom, wait_ms);
+  return r == NB_OK ? r : fail(c, r);
 }
 
 int nb_last_error(nb_ctx* c) { return c ? c->last_error : NB_EINVAL; }

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "force_common.cuh"
+#include "hermite.cuh"
 
 namespace {
 
@@ -378,33 +379,9 @@ __global__ void b_predict(int64_t N, int64_t n_pad, const int32_t* __restrict__ 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int c = cid[i];
     if (nact[c] == 0) continue;
-    const double h = own_time ? 0.0 : tnext[c] - ti[i];
     double px[3], pv[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int64_t q = k * n_pad + i;
-      const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
-      px[k] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
-      pv[k] = vv + h * (av + h * (0.5 * jv));
-    }
-    if (write_fp64) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        xp[k * n_pad + i] = px[k];
-        vp[k * n_pad + i] = pv[k];
-      }
-    }
-    if (write_mixed) {
-      float hi[3], lo[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        hi[k] = __double2float_rn(px[k]);
-        lo[k] = __double2float_rn(px[k] - (double)hi[k]);
-      }
-      jA[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m[i]));
-      jB[i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
-      jC[i] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
-    }
+    nbh::taylor(i, n_pad, own_time ? 0.0 : tnext[c] - ti[i], x, v, a, jk, px, pv);
+    nbh::store_predicted(i, n_pad, px, pv, m[i], xp, vp, jA, jB, jC, write_fp64 != 0, write_mixed != 0);
   }
 }
 
@@ -621,14 +598,6 @@ __global__ void b_tile_boxes(int64_t ntiles, const int32_t* __restrict__ tile_cl
   }
 }
 
-__device__ __forceinline__ double pow2_floor_b(double x) {
-  if (!(x > 0.0)) return 0.0;
-  if (isinf(x)) return x;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  if ((b >> 52) == 0) return 0.0;
-  return __longlong_as_double((long long)(b & 0xFFF0000000000000ULL));
-}
-
 // corrector + block-step rule (Sec. 4.1 step 5), per slot of active clusters
 __global__ void b_correct(int32_t C, int64_t n_pad, const int64_t* __restrict__ citem_off,
                           const int64_t* __restrict__ off, const int32_t* __restrict__ nact,
@@ -648,55 +617,10 @@ __global__ void b_correct(int32_t C, int64_t n_pad, const int64_t* __restrict__ 
     const int64_t s = off[c] + k;
     int64_t i = act[s];
     i = i < 0 ? 0 : (i >= n_pad ? n_pad - 1 : i);
-    const double t = tnext[c];
-    const double h = t - ti[i];
-    const double ih = 1.0 / h;
-    const double ih2 = ih * ih, ih3 = ih2 * ih;
-    const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
-    double na2 = 0, nj2 = 0, n22 = 0, n32 = 0;
-    bool finite = true;
+    double f[7];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int64_t q = r * n_pad + i;
-      const double a0 = a[q], j0 = jk[q];
-      const double a1 = F[r * fstride + s], j1 = F[(3 + r) * fstride + s];
-      const double da = a0 - a1;
-      const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
-      const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
-      const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
-      const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
-      const double a2e = a2 + a3 * h;
-      x[q] = x1;
-      v[q] = v1;
-      a[q] = a1;
-      jk[q] = j1;
-      na2 += a1 * a1;
-      nj2 += j1 * j1;
-      n22 += a2e * a2e;
-      n32 += a3 * a3;
-      finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
-    }
-    const double p1 = F[6 * fstride + s];
-    pot[i] = p1;
-    const double na = sqrt(na2), nj = sqrt(nj2), n2 = sqrt(n22), n3 = sqrt(n32);
-    const double num = na * n2 + nj * nj;
-    const double den = nj * n3 + n2 * n2;
-    const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
-    if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
-    const double dt_old = dt[i];
-    double cnew = pow2_floor_b(crit);
-    cnew = cnew > dt_max ? dt_max : (cnew < dt_min ? dt_min : cnew);
-    double dnew;
-    if (cnew < dt_old) {
-      dnew = cnew;
-    } else {
-      const double two = 2.0 * dt_old;
-      const double qq = t / two;
-      dnew = (cnew >= two && two <= dt_max && qq == floor(qq)) ? two : dt_old;
-    }
-    if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
-    ti[i] = t;
-    dt[i] = dnew;
+    for (int r = 0; r < 7; ++r) f[r] = F[r * fstride + s];
+    nbh::correct_row(i, n_pad, tnext[c], f, eta, dt_min, dt_max, x, v, a, jk, pot, ti, dt, xp, vp, st);
   }
 }
 
@@ -720,9 +644,7 @@ __global__ void b_initial_dt(int64_t N, int64_t n_pad, const double* __restrict_
     pot[i] = F[6 * fstride + i];
     const double nj = sqrt(nj2);
     const double d = (nj > 0.0) ? prm->eta * sqrt(na2) / nj : (double)INFINITY;
-    double cnew = pow2_floor_b(d);
-    cnew = cnew > prm->dt_max ? prm->dt_max : (cnew < prm->dt_min ? prm->dt_min : cnew);
-    dt[i] = cnew;
+    dt[i] = nbh::clamp_dt(nbh::pow2_floor(d), prm->dt_min, prm->dt_max);
     ti[i] = 0.0;
     if (!finite) atomicOr(&st->flags, NB_ST_NUMERIC);
   }

@@ -335,6 +335,10 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 #pragma unroll
     for (int c = 0; c < 7; ++c) NB_ACC_ZERO(k, c);
   }
+  // a warp whose list positions all lie past n computes nothing (nothing of
+  // it is written); it still loads its share of every j-tile.  Small active
+  // blocks leave most warps of an i-tile idle.
+  const bool wact = ibase + (int64_t)(tid & ~31) < n;
   // box of the warp's i-particles (hi parts) and their largest |coordinate|
   float wlo[3], whi[3], wr = 0.0f;
   if (tbox) {
@@ -428,7 +432,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     // Boxes cover NB_BOX_TILE slots: a longer tile needs all of its boxes
     // far, a shorter one uses the box that contains it.
     bool far = false;
-    if (tbox) {
+    if (tbox && wact) {
       constexpr int kBoxes = JT >= NB_BOX_TILE ? JT / NB_BOX_TILE : 1;
       far = true;
 #pragma unroll
@@ -441,6 +445,10 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
         const float lim = kFarTheta * (wr + blo.w);
         far = far && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
       }
+    }
+    if (!wact) {
+      __syncthreads();
+      continue;
     }
     if constexpr (kPk) {
       const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
@@ -521,6 +529,9 @@ __device__ __forceinline__ void fp64_item(Fp64Smem<JT>& sm, const double* __rest
   double hi[7], lo[7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) hi[c] = lo[c] = 0.0;
+  // a warp whose list positions all lie past n computes nothing (its
+  // results are not written); it still loads its share of every j-tile
+  const bool wact = ibase + (int64_t)(tid & ~31) < n;
 
   for (int64_t jt = jlo; jt < jhi; jt += JT) {
     __syncthreads();
@@ -543,6 +554,7 @@ __device__ __forceinline__ void fp64_item(Fp64Smem<JT>& sm, const double* __rest
       }
     }
     __syncthreads();
+    if (!wact) continue;  // the next tile's leading barrier keeps the warp in step
     double p[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) p[c] = 0.0;

@@ -11,12 +11,14 @@ namespace {
 template <int NT, int JT>
 __global__ void __launch_bounds__(NT) force_fp64_kernel(
     const double* __restrict__ xp, const double* __restrict__ vp, const double* __restrict__ m,
-    int64_t n_pad, int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t tiles,
+    int64_t n_pad, int64_t N, const int32_t* __restrict__ list, int64_t n, int64_t tiles,
     double eps2, double* __restrict__ out, int64_t ostride, int finalize) {
   __shared__ nbk::Fp64Smem<JT> sm;
   const int split = blockIdx.y;
+  // j-range of this split, cut at N: the item fills the rest of the last
+  // tile with massless far-away particles, so rows >= N are never read
   const int64_t jlo = nbk::split_begin(split, gridDim.y, tiles) * JT;
-  const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
+  const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, N);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::fp64_item<NT, JT>(sm, xp, vp, m, n_pad, jlo, jhi, list, n, (int64_t)blockIdx.x * NT, eps2, o, ostride,
                          finalize != 0);
@@ -70,7 +72,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
   if (!fin && (int64_t)nsplit * 7 * ostride > c->part_elems) return cudaErrorInvalidValue;
   dim3 grid((unsigned)itiles, (unsigned)nsplit);
   c->launches += fin ? 1 : 2;
-  force_fp64_kernel<NT, JT><<<grid, NT, 0, c->stream>>>(c->xp, c->vp, c->m, c->n_pad, n_j, d_list, n,
+  force_fp64_kernel<NT, JT><<<grid, NT, 0, c->stream>>>(c->xp, c->vp, c->m, c->n_pad, c->n, d_list, n,
                                                         tiles, c->eps * c->eps, out, ostride, fin ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;

@@ -1,0 +1,147 @@
+// hermite.cuh -- per-particle arithmetic of the 4th-order Hermite block-step
+// scheme, shared by every loop driver (the host-driven kernels, the body of
+// the CUDA-graph loop and the persistent loop): the predictor of Sec. 4.1
+// step 3 and the corrector with the power-of-two block-step rule of step 5
+// (block steps of Sec. 2).  One definition, so every driver takes the same
+// steps bit for bit.
+#pragma once
+
+#include <math.h>
+
+#include "nb_internal.cuh"
+
+namespace nbh {
+
+// largest power of two <= x for positive finite x (clears the mantissa)
+__device__ __forceinline__ double pow2_floor(double x) {
+  if (!(x > 0.0)) return 0.0;
+  if (isinf(x)) return x;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b >> 52) == 0) return 0.0;  // subnormal: below any admissible step
+  return __longlong_as_double((long long)(b & 0xFFF0000000000000ULL));
+}
+
+// y / x.  When x is a positive power of two (every block step, and h = t - t_i
+// of every active particle) the quotient is y times 2^-k formed from the
+// exponent bits: the same correctly rounded result without an FP64 divide
+// (the FP64 pipe bounds the corrector).  Anything else takes the division.
+__device__ __forceinline__ double div_pow2(double y, double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long e = b >> 52;  // sign 0 and biased exponent
+  if ((b & 0x000FFFFFFFFFFFFFULL) == 0 && e >= 1 && e <= 2045)
+    return y * __longlong_as_double((long long)((2046ULL - e) << 52));
+  return y / x;
+}
+
+__device__ __forceinline__ double clamp_dt(double c, double dt_min, double dt_max) {
+  if (c > dt_max) c = dt_max;
+  if (c < dt_min) c = dt_min;
+  return c;
+}
+
+// Predictor (Sec. 4.1 step 3) of row i over h = t - t_i, Horner form:
+//   xp = x + v h + a h^2/2 + jk h^3/6,   vp = v + a h + jk h^2/2
+__device__ __forceinline__ void taylor(int64_t i, int64_t n_pad, double h, const double* __restrict__ x,
+                                       const double* __restrict__ v, const double* __restrict__ a,
+                                       const double* __restrict__ jk, double (&px)[3], double (&pv)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t q = d * n_pad + i;
+    const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
+    px[d] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
+    pv[d] = vv + h * (av + h * (0.5 * jv));
+  }
+}
+
+// the predicted row in the FP64 j-store and/or the mixed one; the
+// double-single split of a position is exact: hi = fl32(xp), lo = fl32(xp - hi)
+__device__ __forceinline__ void store_predicted(int64_t i, int64_t n_pad, const double (&px)[3],
+                                                const double (&pv)[3], double mi, double* __restrict__ xp,
+                                                double* __restrict__ vp, float4* __restrict__ jA,
+                                                float4* __restrict__ jB, float2* __restrict__ jC,
+                                                bool write_fp64, bool write_mixed) {
+  if (write_fp64) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xp[d * n_pad + i] = px[d];
+      vp[d * n_pad + i] = pv[d];
+    }
+  }
+  if (write_mixed) {
+    float hi[3], lo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      hi[d] = __double2float_rn(px[d]);
+      lo[d] = __double2float_rn(px[d] - (double)hi[d]);
+    }
+    jA[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(mi));
+    jB[i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
+    jC[i] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
+  }
+}
+
+// Corrector (Sec. 4.1 step 5) of row i at block time t from its new force
+// f = (a1[3], j1[3], pot1), h = t - t_i.  Hermite interpolation of the
+// acceleration through (a0, j0) and (a1, j1) gives at the start
+//   a2 = [-6 (a0 - a1) - h (4 j0 + 2 j1)] / h^2,  a3 = [12 (a0 - a1) + 6 h (j0 + j1)] / h^3,
+// and x1 = xp + a2 h^4/24 + a3 h^5/120,  v1 = vp + a2 h^3/6 + a3 h^4/24.
+// New step: Aarseth criterion at the end of the step (a2e = a2 + a3 h),
+// largest power of two below it within [dt_min, dt_max]; it may shrink
+// freely and doubles only when t is a multiple of the doubled step.
+__device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, const double (&f)[7], double eta,
+                                            double dt_min, double dt_max, double* __restrict__ x,
+                                            double* __restrict__ v, double* __restrict__ a,
+                                            double* __restrict__ jk, double* __restrict__ pot,
+                                            double* __restrict__ ti, double* __restrict__ dt,
+                                            const double* __restrict__ xp, const double* __restrict__ vp,
+                                            nb_dev_status* __restrict__ st) {
+  const double h = t - ti[i];
+  const double ih = div_pow2(1.0, h);
+  const double ih2 = ih * ih, ih3 = ih2 * ih;
+  const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+  double na2 = 0, nj2 = 0, n22 = 0, n32 = 0;
+  bool finite = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int64_t q = c * n_pad + i;
+    const double a0 = a[q], j0 = jk[q];
+    const double a1 = f[c], j1 = f[3 + c];
+    const double da = a0 - a1;
+    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
+    const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
+    const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
+    const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+    const double a2e = a2 + a3 * h;
+    x[q] = x1;
+    v[q] = v1;
+    a[q] = a1;
+    jk[q] = j1;
+    na2 += a1 * a1;
+    nj2 += j1 * j1;
+    n22 += a2e * a2e;
+    n32 += a3 * a3;
+    finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
+  }
+  const double p1 = f[6];
+  pot[i] = p1;
+  const double na = sqrt(na2), nj = sqrt(nj2), n2 = sqrt(n22), n3 = sqrt(n32);
+  const double num = na * n2 + nj * nj;
+  const double den = nj * n3 + n2 * n2;
+  const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
+  if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
+  const double dt_old = dt[i];
+  const double c = clamp_dt(pow2_floor(crit), dt_min, dt_max);
+  double dnew;
+  if (c < dt_old) {
+    dnew = c;
+  } else {
+    const double two = 2.0 * dt_old;
+    const double q = div_pow2(t, two);  // exact: two is a power of two
+    dnew = (c >= two && two <= dt_max && q == floor(q)) ? two : dt_old;
+  }
+  if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
+  ti[i] = t;
+  dt[i] = dnew;
+}
+
+}  // namespace nbh

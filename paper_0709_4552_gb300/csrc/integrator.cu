@@ -4,6 +4,7 @@
 // Sec. 2), initial steps (step 1), energy reduction, and layout helpers.
 #include <math.h>
 
+#include "hermite.cuh"
 #include "nb_internal.cuh"
 
 namespace {
@@ -18,11 +19,9 @@ inline int grid_for(int64_t n, int threads, int cap = 1 << 20) {
 }
 
 // ---------------------------------------------------------------------------
-// Predictor: Taylor expansion to time t (own_time: h = 0, i.e. t = t_i), for
-// i < N; padding particles [N, n_pad) get m = 0 far away.
-//   xp = x + v h + a h^2/2 + jk h^3/6,   vp = v + a h + jk h^2/2
-// FP64 (Horner form); the mixed path's double-single split of xp is exact:
-// hi = fl32(xp), lo = fl32(xp - hi).
+// Predictor (Sec. 4.1 step 3) to time t (own_time: h = 0, i.e. t = t_i), for
+// i < N; padding particles [N, n_pad) get m = 0 far away.  Arithmetic in
+// hermite.cuh.
 // ---------------------------------------------------------------------------
 __global__ void predict_kernel(int64_t N, int64_t n_pad, const double* __restrict__ m,
                                const double* __restrict__ x, const double* __restrict__ v,
@@ -36,62 +35,19 @@ __global__ void predict_kernel(int64_t N, int64_t n_pad, const double* __restric
        i += (int64_t)gridDim.x * blockDim.x) {
     double px[3], pv[3], mi;
     if (i < N) {
-      const double h = own_time ? 0.0 : t - ti[i];
       mi = m[i];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int64_t q = d * n_pad + i;
-        const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
-        px[d] = xv + h * (vv + h * (0.5 * av + h * (jv * (1.0 / 6.0))));
-        pv[d] = vv + h * (av + h * (0.5 * jv));
-      }
+      nbh::taylor(i, n_pad, own_time ? 0.0 : t - ti[i], x, v, a, jk, px, pv);
     } else {
       mi = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) { px[d] = NB_PAD_POS; pv[d] = 0.0; }
     }
-    if (write_fp64) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) { xp[d * n_pad + i] = px[d]; vp[d * n_pad + i] = pv[d]; }
-    }
-    if (write_mixed) {
-      float hi[3], lo[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        hi[d] = __double2float_rn(px[d]);
-        lo[d] = __double2float_rn(px[d] - (double)hi[d]);
-      }
-      jA[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(mi));
-      jB[i] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(pv[0]));
-      jC[i] = make_float2(__double2float_rn(pv[1]), __double2float_rn(pv[2]));
-    }
+    nbh::store_predicted(i, n_pad, px, pv, mi, xp, vp, jA, jB, jC, write_fp64 != 0, write_mixed != 0);
   }
 }
 
-// largest power of two <= x for positive finite x (clears the mantissa).
-__device__ __forceinline__ double pow2_floor_d(double x) {
-  if (!(x > 0.0)) return 0.0;
-  if (isinf(x)) return x;
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  if ((b >> 52) == 0) return 0.0;  // subnormal: below any admissible step
-  return __longlong_as_double((long long)(b & 0xFFF0000000000000ULL));
-}
-
-__device__ __forceinline__ double clamp_dt(double c, double dt_min, double dt_max) {
-  if (c > dt_max) c = dt_max;
-  if (c < dt_min) c = dt_min;
-  return c;
-}
-
-// ---------------------------------------------------------------------------
-// Corrector (Sec. 4.1 step 5): for list position k, particle i = list[k],
-// h = t - t_i; Hermite interpolation of the acceleration through (a0, j0)
-// and (a1, j1) gives at the start
-//   a2 = [-6 (a0 - a1) - h (4 j0 + 2 j1)] / h^2,  a3 = [12 (a0 - a1) + 6 h (j0 + j1)] / h^3,
-// and x1 = xp + a2 h^4/24 + a3 h^5/120,  v1 = vp + a2 h^3/6 + a3 h^4/24.
-// New step: Aarseth criterion at the end of the step (a2e = a2 + a3 h),
-// power-of-two block rule of Sec. 2.
-// ---------------------------------------------------------------------------
+// Corrector and new block step (Sec. 4.1 step 5) for list position k,
+// particle i = list[k], forces F[.][k]; arithmetic in hermite.cuh.
 __global__ void correct_kernel(int64_t n, int64_t n_pad, const int32_t* __restrict__ list,
                                const double* __restrict__ F, int64_t fstride, double t, double eta,
                                double dt_min, double dt_max, double* __restrict__ x,
@@ -103,55 +59,10 @@ __global__ void correct_kernel(int64_t n, int64_t n_pad, const int32_t* __restri
        k += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = list[k];
     i = i < 0 ? 0 : (i >= n_pad ? n_pad - 1 : i);  // never out of bounds on a bad list
-    const double h = t - ti[i];
-    const double ih = 1.0 / h;
-    const double ih2 = ih * ih, ih3 = ih2 * ih;
-    const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
-    double na2 = 0, nj2 = 0, n22 = 0, n32 = 0;
-    bool finite = true;
+    double f[7];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t q = c * n_pad + i;
-      const double a0 = a[q], j0 = jk[q];
-      const double a1 = F[c * fstride + k], j1 = F[(3 + c) * fstride + k];
-      const double da = a0 - a1;
-      const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
-      const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
-      const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
-      const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
-      const double a2e = a2 + a3 * h;
-      x[q] = x1;
-      v[q] = v1;
-      a[q] = a1;
-      jk[q] = j1;
-      na2 += a1 * a1;
-      nj2 += j1 * j1;
-      n22 += a2e * a2e;
-      n32 += a3 * a3;
-      finite = finite && isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
-    }
-    const double p1 = F[6 * fstride + k];
-    pot[i] = p1;
-    const double na = sqrt(na2), nj = sqrt(nj2), n2 = sqrt(n22), n3 = sqrt(n32);
-    const double num = na * n2 + nj * nj;
-    const double den = nj * n3 + n2 * n2;
-    const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
-    if (!(crit >= dt_min)) {
-      if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
-    }
-    const double dt_old = dt[i];
-    double c = clamp_dt(pow2_floor_d(crit), dt_min, dt_max);
-    double dnew;
-    if (c < dt_old) {
-      dnew = c;
-    } else {
-      const double two = 2.0 * dt_old;
-      const double q = t / two;  // exact: two is a power of two
-      dnew = (c >= two && two <= dt_max && q == floor(q)) ? two : dt_old;
-    }
-    if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
-    ti[i] = t;
-    dt[i] = dnew;
+    for (int c = 0; c < 7; ++c) f[c] = F[c * fstride + k];
+    nbh::correct_row(i, n_pad, t, f, eta, dt_min, dt_max, x, v, a, jk, pot, ti, dt, xp, vp, st);
   }
 }
 
@@ -177,7 +88,7 @@ __global__ void initial_dt_kernel(int64_t N, int64_t n_pad, const double* __rest
     pot[i] = F[6 * fstride + i];
     const double nj = sqrt(nj2);
     const double d = (nj > 0.0) ? eta * sqrt(na2) / nj : (double)INFINITY;
-    dt[i] = clamp_dt(pow2_floor_d(d), dt_min, dt_max);
+    dt[i] = nbh::clamp_dt(nbh::pow2_floor(d), dt_min, dt_max);
     ti[i] = 0.0;
     if (!finite) atomicOr(&st->flags, NB_ST_NUMERIC);
   }

@@ -127,6 +127,7 @@ struct nb_ctx {
   int64_t* h_offsets;
   double* h_ceps;
   void* ens;            // ensemble work area (ensemble.cu)
+  void* loop;           // persistent-loop work area (persistent.cu)
 };
 
 // ---- launchers (integrator.cu) -------------------------------------------
@@ -183,6 +184,12 @@ void nb_ensemble_free(nb_ctx* c);
 // (re)compute the spatial order within each cluster when it is due (mixed ensembles)
 int nb_ensemble_ensure_sorted(nb_ctx* c);
 int nb_integrate_graph(nb_ctx* c, double t_end);
+
+// persistent.cu: the block-step loop of one system as one cooperative launch
+int nb_integrate_persistent(nb_ctx* c, double t_end);
+void nb_persistent_free(nb_ctx* c);
+// the grid barrier's bounded wait (phantom: wait for one CTA more than launched)
+int nb_persistent_barrier_check(nb_ctx* c, int phantom, double wait_ms);
 
 // ---- device helpers ---------------------------------------------------------
 // the low 10 bits of a moved to every third bit (one axis of a Morton code)

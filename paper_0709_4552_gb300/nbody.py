@@ -22,13 +22,16 @@ NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ENUMERIC, NB_EDTMIN, NB_ETIMEOUT, NB_E
 NB_FP64, NB_MIXED = 0, 1
 NB_PTR_HOST, NB_PTR_DEVICE = 0, 1
 NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
+NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT = 0, 1, 2
+NB_PERSISTENT_MAX_N = 65536
 
 # every symbol include/nbody.h declares
 EXPORTS = (
     "nb_create", "nb_destroy", "nb_set_params", "nb_get_params", "nb_default_params", "nb_set_precision",
     "nb_set_j_particles", "nb_set_n", "nb_get_n", "nb_get_particles", "nb_next_block", "nb_predict",
     "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
-    "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_last_error", "nb_clear_error",
+    "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
+    "nb_last_error", "nb_clear_error",
     "nb_set_tuning", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
@@ -82,6 +85,7 @@ def lib():
         "nb_get_timings": (_int, [_vp, _pd, _pd, _pd, _pd, _int]),
         "nb_get_counters": (_int, [_vp, _pi64, _pi64]),
         "nb_check_device_status": (_int, [_vp, _pi64]),
+        "nb_check_grid_barrier": (_int, [_vp, _int, _d]),
         "nb_last_error": (_int, [_vp]),
         "nb_clear_error": (None, [_vp]),
         "nb_set_tuning": (_int, [_vp, _int, _int, _int, _int]),
@@ -277,8 +281,12 @@ def nb_step(ctx):
     return t.value, n.value
 
 
-def nb_integrate(ctx, t_end, use_graph=False):
-    _check(lib().nb_integrate(ctx, float(t_end), int(bool(use_graph))), "nb_integrate")
+def nb_integrate(ctx, t_end, use_graph=False, loop=None):
+    """Block steps to t_end.  loop: NB_LOOP_HOST, NB_LOOP_GRAPH or
+    NB_LOOP_PERSISTENT; without it, use_graph picks the graph or host loop."""
+    if loop is None:
+        loop = NB_LOOP_GRAPH if use_graph else NB_LOOP_HOST
+    _check(lib().nb_integrate(ctx, float(t_end), int(loop)), "nb_integrate")
 
 
 def nb_energy(ctx):
@@ -304,6 +312,12 @@ def nb_check_device_status(ctx):
     u = _i64()
     code = lib().nb_check_device_status(ctx, ctypes.byref(u))
     return code, u.value
+
+
+def nb_check_grid_barrier(ctx, phantom=False, wait_ms=100.0):
+    """Status code of the persistent loop's bounded grid-barrier wait on the
+    device (NB_ETIMEOUT expected with phantom=True) -- does not raise."""
+    return lib().nb_check_grid_barrier(ctx, int(bool(phantom)), float(wait_ms))
 
 
 def nb_last_error(ctx):

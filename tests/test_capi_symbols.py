@@ -39,6 +39,18 @@ def test_binding_covers_every_symbol():
     assert sorted(nbody.EXPORTS) == _declared()
 
 
+def test_binding_constants_match_header():
+    from paper_0709_4552_gb300 import nbody
+    src = open(os.path.join(ROOT, "include", "nbody.h")).read()
+    defs = dict(re.findall(r"#define\s+(NB_[A-Z0-9_]+)\s+(-?\d+)\b", src))
+    names = [n for n in defs if hasattr(nbody, n)]
+    for must in ("NB_OK", "NB_ETIMEOUT", "NB_FP64", "NB_MIXED", "NB_LOOP_HOST", "NB_LOOP_GRAPH",
+                 "NB_LOOP_PERSISTENT", "NB_PERSISTENT_MAX_N", "NB_ENSEMBLE_PER_CLUSTER"):
+        assert must in names
+    for n in names:
+        assert getattr(nbody, n) == int(defs[n]), n
+
+
 def test_host_only_calls(lib):
     from paper_0709_4552_gb300 import nbody as nb
     assert nb.nb_version().startswith("libnbody")
