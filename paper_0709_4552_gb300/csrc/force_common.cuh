@@ -335,10 +335,6 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 #pragma unroll
     for (int c = 0; c < 7; ++c) NB_ACC_ZERO(k, c);
   }
-  // a warp whose list positions all lie past n computes nothing (nothing of
-  // it is written); it still loads its share of every j-tile.  Small active
-  // blocks leave most warps of an i-tile idle.
-  const bool wact = ibase + (int64_t)(tid & ~31) < n;
   // box of the warp's i-particles (hi parts) and their largest |coordinate|
   float wlo[3], whi[3], wr = 0.0f;
   if (tbox) {
@@ -432,7 +428,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     // Boxes cover NB_BOX_TILE slots: a longer tile needs all of its boxes
     // far, a shorter one uses the box that contains it.
     bool far = false;
-    if (tbox && wact) {
+    if (tbox) {
       constexpr int kBoxes = JT >= NB_BOX_TILE ? JT / NB_BOX_TILE : 1;
       far = true;
 #pragma unroll
@@ -445,10 +441,6 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
         const float lim = kFarTheta * (wr + blo.w);
         far = far && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= lim * lim;
       }
-    }
-    if (!wact) {
-      __syncthreads();
-      continue;
     }
     if constexpr (kPk) {
       const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
