@@ -50,6 +50,23 @@ def test_persistent_fp64_matches_host_loop(nbl, N):
     assert cb["kernel_launches"] == 1   # one cooperative launch for the whole run
 
 
+@pytest.mark.parametrize("N", [2, 3, 17, 64, 100, 128])
+def test_loops_bitwise_equal_when_sums_group_alike(nbl, N):
+    # with at most two j-splits every driver sums the same partials in the
+    # same order, so the three loops share predictor, forces, corrector and
+    # block rule bit for bit (one 64-particle j-tile: all three; two: host
+    # and persistent)
+    ics = inputs.plummer(N, 640 + N, "salpeter")
+    eps, t_end = 1 / 256, 2.0 ** -5
+    runs = [nbl.NB_LOOP_HOST, nbl.NB_LOOP_PERSISTENT] + ([nbl.NB_LOOP_GRAPH] if N <= 64 else [])
+    out = [_run(nbl, nbl.NB_FP64, ics, eps, t_end, [(t_end, loop)]) for loop in runs]
+    (a, ca) = out[0]
+    for b, cb in out[1:]:
+        assert cb["block_steps"] == ca["block_steps"]
+        for k in ("x", "v", "a", "jerk", "pot", "t", "dt"):
+            assert np.array_equal(a[k], b[k]), k
+
+
 @pytest.mark.parametrize("N", [1500, 6000])
 def test_persistent_mixed_matches_host_loop(nbl, N):
     # several launches: the spatial order is renewed every 64 block steps
