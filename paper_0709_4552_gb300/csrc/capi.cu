@@ -633,7 +633,7 @@ int nb_integrate(nb_ctx* c, double t_end, int loop) {
   int r = loop == NB_LOOP_GRAPH        ? nb_integrate_graph(c, t_end)
           : loop == NB_LOOP_PERSISTENT ? nb_integrate_persistent(c, t_end)
                                        : integrate_host_loop(c, t_end);
-  if (r) return r;
+  if (r) return fail(c, r);
   r = device_status_code(c, nullptr);
   if (r == NB_ENUMERIC || r == NB_ETIMEOUT) return fail(c, r);
   return NB_OK;
