@@ -66,6 +66,9 @@ def test_null_arguments_rejected(lib):
     assert L.nb_create(None, 10, 0, 0, None) == nb.NB_EINVAL
     assert L.nb_set_params(None, 0.1, 0.01, 2.0 ** -22, 0.125) == nb.NB_EINVAL
     assert L.nb_step(None, None, None) == nb.NB_EINVAL
+    for loop in (nb.NB_LOOP_HOST, nb.NB_LOOP_GRAPH, nb.NB_LOOP_PERSISTENT):
+        assert L.nb_integrate(None, 0.125, loop) == nb.NB_EINVAL
+    assert L.nb_check_grid_barrier(None, 1, 50.0) == nb.NB_EINVAL
     h = ctypes.c_void_p()
     assert L.nb_create(ctypes.byref(h), 0, 0, 0, None) == nb.NB_EINVAL       # n_max < 1
     assert L.nb_create(ctypes.byref(h), 10, 7, 0, None) == nb.NB_EINVAL      # bad precision
