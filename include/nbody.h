@@ -192,8 +192,8 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  *   NB_LOOP_GRAPH       one CUDA graph whose body sits in a device-side while
  *                       node (no host round trip per step);
  *   NB_LOOP_PERSISTENT  one cooperative kernel that stays resident for the
- *                       whole run (one CTA group per SM, three grid barriers
- *                       per block step, each wait bounded), for systems whose
+ *                       whole run (a few CTAs per SM, three grid barriers per
+ *                       block step, each wait bounded), for systems whose
  *                       block steps are latency-bound: N <= NB_PERSISTENT_MAX_N.
  * All three take the same block steps with the same per-particle arithmetic;
  * sums over j-splits may group differently.  The mixed path renews its
