@@ -27,7 +27,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -59,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="sampled i for the oracle legs (the reference arm takes a quarter per step)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--strict-steps", type=int, default=2,
+                    help="block steps timed again with the far-tile pass off (roofline_strict; 0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", default="", help="force launch override ipt,threads,jtile,nsplit (0 = auto)")
     ap.add_argument("--workload", default="c3",
@@ -150,9 +151,10 @@ def fp32_peak_tflops(sms, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-# the committed ncu summary of the mixed force kernel on this benchmark's full
-# launch; its DRAM bytes count only while the kernel source is the one profiled
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "force_mixed_kernel_bench_n1048576.md")
+# the committed ncu record (JSON beside its Markdown summary) of the mixed force
+# kernel on this benchmark's full launch; its DRAM bytes count only while the
+# kernel source is the one profiled
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "force_mixed_kernel_bench_n1048576.json")
 KERNEL_SOURCES = ("paper_0709_4552_gb300/csrc/force_common.cuh", "paper_0709_4552_gb300/csrc/force_mixed.cu")
 
 
@@ -166,18 +168,15 @@ def kernel_source_digest():
 
 def profiled_traffic(n):
     """DRAM bytes (read + write) of one mixed force launch over all n particles, from
-    the committed ncu summary, or None when there is none for n or the kernel changed."""
+    the committed ncu record, or None when there is none for n or the kernel changed."""
     try:
         with open(TRAFFIC_PROFILE) as f:
-            text = f.read()
-    except OSError:
+            rec = json.load(f)
+        if int(rec["particles"]) != n or rec["kernel_source_sha256_16"] != kernel_source_digest():
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
         return None
-    dig = re.search(r"^kernel_source_sha256_16: ([0-9a-f]+)\s*$", text, re.M)
-    num = re.search(r"^dram_bytes_per_launch: (\d+)\s*$", text, re.M)
-    size = re.search(r"^particles: (\d+)\s*$", text, re.M)
-    if not (dig and num and size) or int(size.group(1)) != n or dig.group(1) != kernel_source_digest():
-        return None
-    return int(num.group(1))
 
 
 def measured_hbm_gbs():
@@ -628,6 +627,27 @@ def main():
         phases[name] = {"ms": ms_k, "bytes": b, "achieved_gbs": gbs, "peak_gbs": hbm,
                         "frac": (gbs / hbm) if (gbs and hbm) else None, "bound": "fp64 pipe"}
 
+    # the same block steps with the far-tile pass off (double-single position
+    # differences on every tile: the strict form of the precision pattern),
+    # timed the same way, beside the default
+    strict = None
+    if prec == nb.NB_MIXED and args.strict_steps > 0:
+        s.set_far_tiles(False)
+        s.get_timings(reset=True)
+        for _ in range(args.strict_steps):
+            flush.fill_(1.0)
+            s.step()
+        barrier()
+        tim_s = s.get_timings(reset=True)
+        s.set_far_tiles(True)
+        strict_s = tim_s["ms_force"] / 1e3 / args.strict_steps
+        strict_tflops = FLOP_PER_INTERACTION * float(N) * N / strict_s / 1e12
+        strict = {"bound": "alu", "achieved": strict_tflops, "peak": peak, "unit": "TFLOP/s",
+                  "frac": strict_tflops / peak, "ms_per_launch": strict_s * 1e3,
+                  "launches": args.strict_steps, "far_tiles": False,
+                  "default_ms_per_launch": force_s_per_launch * 1e3,
+                  "far_pass_speedup": strict_s / force_s_per_launch}
+
     # end to end through the C ABI with host buffers: H2D of the step's inputs,
     # the step, D2H of its results, all inside the timed region
     e2e = None
@@ -661,6 +681,10 @@ def main():
         t_now = float(st["t"][0])
         s.predict(t_now)
         am, jm, pm = s.compute_forces(idx)
+        if prec == nb.NB_MIXED:
+            s.set_far_tiles(False)
+            as_, js_, ps_ = s.compute_forces(idx)
+            s.set_far_tiles(True)
         s.set_precision(nb.NB_FP64)
         s.predict(t_now)
         torch.cuda.synchronize(dev)
@@ -710,7 +734,13 @@ def main():
                 "sample": k, "mixed_acc_median": float(np.median(ea)), "mixed_acc_max": float(ea.max()),
                 "mixed_jerk_median": float(np.median(ej)), "mixed_jerk_max": float(ej.max()),
                 "mixed_pot_median": float(np.median(ep)), "mixed_pot_max": float(ep.max()),
-                "fp64_acc_max": float(e64.max())}
+                "fp64_acc_max": float(e64.max()), "fp64_jerk_max": float(rel(j64, jr).max()),
+                "fp64_pot_max": float((np.abs(p64 - pr) / np.abs(pr)).max())}
+            if prec == nb.NB_MIXED:
+                es = (rel(as_, ar), rel(js_, jr), np.abs(ps_ - pr) / np.abs(pr))
+                for nm, e_ in zip(("acc", "jerk", "pot"), es):
+                    extra["accuracy_vs_oracle"][f"strict_{nm}_median"] = float(np.median(e_))
+                    extra["accuracy_vs_oracle"][f"strict_{nm}_max"] = float(e_.max())
     s.close()
 
     if rank == 0:
@@ -732,6 +762,7 @@ def main():
                                         + ("" if fp_div == 1.0 else " / 64 (FP64 pipe)")),
                          "frac_at_sampled_clock": (achieved_tflops * fp_div / fp32_peak_tflops(sms, sm_mhz))
                          if sm_mhz else None},
+            "roofline_strict": strict,
             "hbm_rooflines": phases,
             "phases_ms_per_step": {"predict": tim["ms_pred"] / args.steps, "force": tim["ms_force"] / args.steps,
                                    "correct": tim["ms_corr"] / args.steps},

@@ -49,9 +49,15 @@ extern "C" {
 #define NB_ESTATE    -7   /* call out of order (e.g. forces before predict) */
 
 /* ---- force-path precision ---------------------------------------------- */
-#define NB_FP64   0  /* IEEE FP64 pairwise arithmetic                        */
-#define NB_MIXED  1  /* FP32 pairwise on double-single position differences,
-                        FP64 accumulation of FP32 partial sums               */
+#define NB_FP64   0  /* IEEE FP64 pairwise arithmetic; 1/s from an FP32 seed
+                        refined in FP64 (any s^2 > 0; s^2 = 0 only for the
+                        self pair, which is excluded by index)                 */
+#define NB_MIXED  1  /* FP32 pairwise arithmetic on double-single position
+                        differences; the FP32 sum over each j-tile is folded
+                        into a double-single (FP32 hi + lo, TwoSum)
+                        accumulator; results converted to FP64.  Pair
+                        distances must lie in the FP32 normal range
+                        (s^2 >= 2^-126), which any eps >= 2^-63 ensures       */
 
 /* ---- where caller buffers live ---------------------------------------- */
 #define NB_PTR_HOST    0
@@ -262,6 +268,24 @@ void nb_clear_error(nb_ctx* ctx);
 int nb_set_tuning(nb_ctx* ctx, int i_per_thread, int threads, int j_tile, int n_split);
 
 /*
+ * nb_set_far_tiles -- the mixed path's far-tile pass (not in the paper).
+ * With the particles kept in spatial order, a (warp of i, j-tile) pair whose
+ * bounding boxes are at least theta (|x|max_i + |x|max_j) apart (theta = 1/8)
+ * forms each position difference from the FP32 "hi" parts alone, with
+ * relative error <= 2^-24 (1/theta + 1) ~ 5.4e-7 per pair; every other pair,
+ * and every pair when the pass is off, uses the double-single difference
+ * (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo).  enable != 0 turns the pass on (the
+ * default), 0 off ("strict": double-single differences on every tile, at
+ * about 6 more FP32 operations per pair).  Applies to every later force
+ * launch of the context (host, graph and persistent loops, ensembles); the
+ * FP64 path ignores it.  Errors: NB_EINVAL (ctx NULL).
+ */
+int nb_set_far_tiles(nb_ctx* ctx, int enable);
+
+/* nb_get_far_tiles -- whether the far-tile pass is on (1) or off (0). */
+int nb_get_far_tiles(nb_ctx* ctx, int* enabled);
+
+/*
  * nb_autotune -- time the supported force launches for the current N and
  * active-block size n on the current state (needs a prediction) and keep the
  * fastest for blocks of about that size.  Writes the chosen configuration
@@ -329,8 +353,11 @@ int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
  * the n active particles i_idx[0..n) from all N particles, with every buffer
  * owned by the caller and resident on the current CUDA device: m[N],
  * x[N][3], v[N][3] (positions/velocities at the common time), i_idx[n]
- * (int32, each in [0, N)), outputs acc[n][3], jerk[n][3], pot[n] (any may be
- * NULL).  Work is enqueued on cuda_stream (a cudaStream_t, NULL = default
+ * (int32, each in [0, N); the list need not be sorted), outputs acc[n][3],
+ * jerk[n][3], pot[n] (any may be NULL).  The indices are not checked (that
+ * would need a status word the caller reads back): an index below 0 or
+ * >= N is clamped to 0 or N - 1 for every read, so no access leaves the
+ * caller's arrays, and the outputs at that list position are unspecified.  Work is enqueued on cuda_stream (a cudaStream_t, NULL = default
  * stream); the call returns without synchronising.  It calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *
@@ -339,7 +366,10 @@ int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
  * library until the process exits).  The first call on a device does a
  * one-time set-up: it looks up that array's device address
  * (cudaGetSymbolAddress) with the device current.  Make that first call
- * before any stream capture.  All calls share the array, which keeps the
+ * before any stream capture.  The address is remembered with the id of the
+ * CUDA context it belongs to; after a device reset the next call repeats the
+ * look-up (so, after a reset, make one call before any capture again).  All
+ * calls share the array, which keeps the
  * previous call's contents (every partial is written before it is read, so
  * nothing needs clearing): calls whose work may overlap on the GPU race and
  * must be ordered by the caller (one stream, or events).

@@ -340,6 +340,7 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
   c->n_pad = ((n_max + NB_JPAD - 1) / NB_JPAD) * NB_JPAD;
   c->sel_ctas = 1024;
   c->sort_interval = 64;
+  c->far_tiles = 1;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = sms > 0 ? sms : 1;
@@ -712,6 +713,18 @@ int nb_set_tuning(nb_ctx* c, int i_per_thread, int threads, int j_tile, int n_sp
     if (!nb_tuning_supported(c->precision, full)) return fail(c, NB_EINVAL);
   }
   c->tune_override = t;
+  return NB_OK;
+}
+
+int nb_set_far_tiles(nb_ctx* c, int enable) {
+  if (!c) return NB_EINVAL;
+  c->far_tiles = enable ? 1 : 0;
+  return NB_OK;
+}
+
+int nb_get_far_tiles(nb_ctx* c, int* enabled) {
+  if (!c || !enabled) return NB_EINVAL;
+  *enabled = c->far_tiles;
   return NB_OK;
 }
 

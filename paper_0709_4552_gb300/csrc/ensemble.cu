@@ -844,7 +844,7 @@ void launch_force(nb_ctx* c, Batch* b, bool mixed) {
     b_force_mixed<NT, kMixIPT, kMixJT><<<b->grid_mixed, NT, 0, c->stream>>>(
         b->C, b->off, b->eps2f, c->n_pad, c->jA, c->jB, c->jC, c->act, b->nact, b->itiles, b->nsplit, b->jps,
         b->item_off, b->part_off, b->pstride, c->F, c->n_pad, c->part,
-        single_boxes(c, b) ? c->tbox : (cluster_boxes(c, b) ? b->tbox : nullptr),
+        !c->far_tiles ? nullptr : single_boxes(c, b) ? c->tbox : (cluster_boxes(c, b) ? b->tbox : nullptr),
         cluster_boxes(c, b) ? b->tile_off : nullptr, b->wq);
   else
     b_force_fp64<NT, kF64JT><<<b->grid_fp64, NT, 0, c->stream>>>(

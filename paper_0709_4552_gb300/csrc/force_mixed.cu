@@ -55,8 +55,9 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
   double* out = fin ? c->F : c->part;
   if (!fin && (int64_t)nsplit * 7 * ostride > c->part_elems) return cudaErrorInvalidValue;
   c->launches += fin ? 1 : 2;
-  // resident spatial order: far-tile boxes when the tiles match
-  const float4* tbox = c->perm_valid ? c->tbox : nullptr;
+  // resident spatial order: far-tile boxes when the tiles match (unless the
+  // context asks for double-single differences on every tile)
+  const float4* tbox = (c->perm_valid && c->far_tiles) ? c->tbox : nullptr;
   force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n, tiles,
                                                               eps2, out, ostride, fin ? 1 : 0, tbox, ord);
   cudaError_t e = cudaGetLastError();

@@ -115,6 +115,9 @@ struct nb_ctx {
   bool ev_pending;           // step events recorded but not yet read
   int64_t launches;          // kernels launched by this context (all launchers)
   int64_t steps;             // block steps taken
+  // mixed path: hi-only differences on (warp, j-tile) pairs that pass the
+  // far test (1, the default), or double-single differences everywhere (0)
+  int far_tiles;
   // tuning
   nb_tuning tune_override;   // all-zero = automatic
   nb_tune_entry tune_table[16];
@@ -208,12 +211,19 @@ __device__ __forceinline__ float nb_rsqrt_approx(float x) {
   return y;
 }
 
-// 1/sqrt(x) in FP64 for x in the float normal range: FP32 hardware seed
-// refined by one 2nd-order Newton-Raphson (Householder) step,
+// 1/sqrt(x) in FP64 for any x >= 0.  For x in the FP32 normal range
+// [2^-126, 2^128) the FP32 hardware seed is refined by one 2nd-order
+// Newton-Raphson (Householder) step,
 //   e = 1 - x y0^2,  y = y0 (1 + e/2 + 3 e^2 / 8),
-// whose relative error is O(e^3) ~ 2^-63 for |e| <= 2^-21.
+// whose relative error is O(e^3) ~ 2^-63 for |e| <= 2^-21.  Outside that
+// range the seed is 0 or Inf (the FP32 conversion overflows, or underflows
+// and is flushed), and CUDA's double-precision rsqrt takes over: x = 0 gives
+// +Inf, x = Inf gives 0, tiny and huge finite x their correctly scaled
+// values.  The test costs two FP32 compares per call, off the FP64 pipe.
 __device__ __forceinline__ double nb_rsqrt_fp64(double x) {
-  const double y0 = (double)nb_rsqrt_approx((float)x);
+  const float s = nb_rsqrt_approx((float)x);
+  if (!(s > 0.0f && s < __int_as_float(0x7f800000))) return rsqrt(x);
+  const double y0 = (double)s;
   const double e = fma(-x, y0 * y0, 1.0);
   return fma(y0 * e, fma(0.375, e, 0.5), y0);
 }

@@ -14,7 +14,11 @@
 // that array's name as a device address, so the first call on each device
 // looks the address up with cudaGetSymbolAddress while that device is current
 // and keeps it (a one-time set-up; make that first call before any stream
-// capture).  Every call shares the array and it keeps the previous call's
+// capture).  The address is kept together with the unique id of the CUDA
+// context it was looked up in: after a device reset (a new primary context,
+// where the module and its array may be loaded elsewhere) the next call sees
+// a different id and looks the address up again instead of writing to a
+// freed one.  Every call shares the array and it keeps the previous call's
 // contents; the kernels write every partial they later read, so nothing has to
 // start at zero.  Calls whose work overlaps on the GPU (different streams, no
 // ordering between them) race on the array and must not be issued.
@@ -31,7 +35,36 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) double g_scratch[NB_NOALLOC_SCRATCH_DOUBLES];
 
 std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices];  // device address of g_scratch, per device
+double* g_scratch_ptr[kMaxDevices];               // device address of g_scratch, per device
+unsigned long long g_scratch_ctx[kMaxDevices];    // id of the context it belongs to
+
+// the current CUDA context's unique id (driver API, reached through the
+// runtime's entry-point query so the library needs no link to libcuda);
+// 0 when it cannot be read, which forces a fresh look-up on every call
+unsigned long long current_context_id() {
+  typedef int (*get_current_fn)(void**);
+  typedef int (*get_id_fn)(void*, unsigned long long*);
+  static get_current_fn get_current = nullptr;
+  static get_id_fn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (get_current_fn)f1;
+      get_id = (get_id_fn)f2;
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Same pairwise sums as the library's FP64 path (Sec. 4.1 step 4, Eq. 3),
 // reading row-major [N][3] caller arrays: CTA (x, y) = (i-tile, j-split);
@@ -133,11 +166,16 @@ int scratch_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NB_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long ctx_id = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx_id == 0 || ctx_id != g_scratch_ctx[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) return NB_ECUDA;
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return NB_ECUDA;
+    }
     g_scratch_ptr[dev] = (double*)p;
+    g_scratch_ctx[dev] = ctx_id;
   }
   *out = g_scratch_ptr[dev];
   return NB_OK;

@@ -591,7 +591,7 @@ int nb_integrate_persistent(nb_ctx* c, double t_end) {
     p.jA = c->jA;
     p.jB = c->jB;
     p.jC = c->jC;
-    p.tbox = mixed && c->perm_valid ? c->tbox : nullptr;
+    p.tbox = mixed && c->perm_valid && c->far_tiles ? c->tbox : nullptr;
     p.act = c->act;
     p.F = c->F;
     p.part = c->part;

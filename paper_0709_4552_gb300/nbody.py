@@ -32,7 +32,7 @@ EXPORTS = (
     "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
-    "nb_set_tuning", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
+    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
 
@@ -89,6 +89,8 @@ def lib():
         "nb_last_error": (_int, [_vp]),
         "nb_clear_error": (None, [_vp]),
         "nb_set_tuning": (_int, [_vp, _int, _int, _int, _int]),
+        "nb_set_far_tiles": (_int, [_vp, _int]),
+        "nb_get_far_tiles": (_int, [_vp, _pint]),
         "nb_autotune": (_int, [_vp, _i64, _pint, _pint, _pint, _pint]),
         "nb_ensemble_create": (_int, [ctypes.POINTER(_vp), _i32, _vp, _vp, _int, _int, _vp]),
         "nb_measure_peaks": (_int, [_vp, _pd, _pd, _pd]),
@@ -330,6 +332,16 @@ def nb_clear_error(ctx):
 
 def nb_set_tuning(ctx, i_per_thread=0, threads=0, j_tile=0, n_split=0):
     _check(lib().nb_set_tuning(ctx, int(i_per_thread), int(threads), int(j_tile), int(n_split)), "nb_set_tuning")
+
+
+def nb_set_far_tiles(ctx, enable=True):
+    _check(lib().nb_set_far_tiles(ctx, int(bool(enable))), "nb_set_far_tiles")
+
+
+def nb_get_far_tiles(ctx):
+    v = _int()
+    _check(lib().nb_get_far_tiles(ctx, ctypes.byref(v)), "nb_get_far_tiles")
+    return bool(v.value)
 
 
 def nb_autotune(ctx, n):

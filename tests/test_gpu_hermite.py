@@ -99,9 +99,14 @@ def test_config1_shared_steps(nbl, prec):
                 s.predict(t)
                 a, j, p = s.compute_forces(np.arange(N, dtype=np.int32))
                 ar, jr, pr = oracle.forces(m, st["x"], st["v"], eps, compensated=True)
-                tol = 1e-12 if P == nbl.NB_FP64 else 1e-5
-                assert rel_vec(a, ar).max() < tol and rel_vec(j, jr).max() < tol * 10
-                assert rel_scalar(p, pr).max() < tol
+                errs = {"acc": rel_vec(a, ar), "jerk": rel_vec(j, jr), "pot": rel_scalar(p, pr)}
+                for name, e in errs.items():
+                    if P == nbl.NB_FP64:
+                        assert e.max() <= 1e-12, (k, name, e.max())
+                    else:
+                        # the mixed path's bounds: median <= 1e-6, max <= 1e-5
+                        assert np.median(e) <= 1e-6, (k, name, np.median(e))
+                        assert e.max() <= 1e-5, (k, name, e.max())
         st = _state(s, N)
     dE_gpu = abs(_energy(m, st, eps) - E0) / abs(E0)
     print(f"config1 {prec}: |dE/E| gpu {dE_gpu:.3e} oracle {dE_orc:.3e}")
@@ -110,6 +115,45 @@ def test_config1_shared_steps(nbl, prec):
     assert np.abs(P_mom).max() < (1e-14 if P == nbl.NB_FP64 else 1e-9)
     if P == nbl.NB_FP64:
         assert np.abs(st["x"] - r["x"]).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_timings_count_interactions(nbl, prec):
+    # nb_get_timings: the interaction count is the sum of n N over the block
+    # steps (Eq. 3's n N per force call), and every phase took device time
+    P = nbl.NB_FP64 if prec == "fp64" else nbl.NB_MIXED
+    N = 2000
+    m, x, v = inputs.plummer(N, 207, "salpeter")
+    with _ctx(nbl, m, x, v, 1 / 256, 0.01, 2.0 ** -22, 2.0 ** -3, prec=P) as s:
+        tim = s.get_timings(reset=True)
+        assert tim["interactions"] == float(N) * N   # the initial full i = j evaluation
+        assert s.get_timings()["interactions"] == 0.0
+        total, c0 = 0, s.get_counters()
+        for _ in range(25):
+            t, n = s.step()
+            total += n * N
+        tim = s.get_timings(reset=True)
+        c1 = s.get_counters()
+        assert c1["block_steps"] - c0["block_steps"] == 25
+        assert tim["interactions"] == float(total)
+        assert tim["ms_pred"] > 0 and tim["ms_force"] > 0 and tim["ms_corr"] > 0
+        if P != nbl.NB_FP64:
+            return
+        # host-loop integration: n N per block step, checked against a replay
+        # of the same steps through nb_step (FP64: the replay takes the same
+        # steps bit for bit)
+        st = _state(s, N)
+        s.integrate(2.0 ** -3)
+        tim = s.get_timings(reset=True)
+        replay = 0
+        with _ctx(nbl, m, x, v, 1 / 256, 0.01, 2.0 ** -22, 2.0 ** -3, prec=P, state=st) as r:
+            while True:
+                t, n_next, _ = r.next_block(want_indices=False)
+                if t > 2.0 ** -3:
+                    break
+                t, n = r.step()
+                replay += n * N
+        assert tim["interactions"] == float(replay)
 
 
 def _kepler():

@@ -154,3 +154,25 @@ def test_grid_barrier_wait_is_bounded(nbl):
         assert s.check_device_status()[0] == nbl.NB_OK
         s.integrate(2.0 ** -6, loop=nbl.NB_LOOP_PERSISTENT)
         assert np.all(s.get_particles(0, 256)["t"] == 2.0 ** -6)
+
+
+@pytest.mark.parametrize("loop", ["graph", "persistent"])
+def test_strict_differences_in_every_loop(nbl, loop):
+    # nb_set_far_tiles(0) reaches the graph and persistent loops' force items:
+    # they follow the strict host loop as closely as the default ones do
+    N, eps, t_end = 6000, 1 / 256, 2.0 ** -5
+    m, x, v = inputs.plummer(N, 700 + N, "salpeter")
+    L = nbl.NB_LOOP_GRAPH if loop == "graph" else nbl.NB_LOOP_PERSISTENT
+    out = []
+    for lp in (nbl.NB_LOOP_HOST, L):
+        with _single(nbl, nbl.NB_MIXED, m, x, v, eps, 2.0 ** -22, t_end) as s:
+            s.set_far_tiles(False)
+            c0 = s.get_counters()
+            s.integrate(t_end, loop=lp)
+            c1 = s.get_counters()
+            out.append((s.get_particles(0, N), c1["block_steps"] - c0["block_steps"]))
+    (a, ca), (b, cb) = out
+    assert np.all(a["t"] == t_end) and np.all(b["t"] == t_end)
+    assert abs(cb - ca) <= 0.05 * ca
+    assert np.mean(a["dt"] == b["dt"]) > 0.95
+    assert np.abs(a["x"] - b["x"]).max() < 1e-5
