@@ -147,6 +147,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def sec41_taus(t_pred, t_force, t_corr, N, steps, interactions, particle_steps):
+    """Per-unit costs of Sec. 4.1 from measured phase times: t_pred = tau_pred N per
+    block step (Eq. 2), t_force = tau_force n N (Eq. 3), t_corr = tau_corr n (Eq. 4),
+    summed over the steps (interactions = sum n N, particle_steps = sum n)."""
+    return t_pred / (steps * N), t_force / interactions, t_corr / particle_steps
+
+
+def sec41_T(taus, N, steps, interactions, particle_steps):
+    """Eq. 1: T_integrate = sum over the block steps of (tau_pred N + tau_force n N +
+    tau_corr n), written with the sums of n N and n over the steps."""
+    tau_pred, tau_force, tau_corr = taus
+    return tau_pred * N * steps + tau_force * interactions + tau_corr * particle_steps
+
+
 def fp32_peak_tflops(sms, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
@@ -395,48 +409,78 @@ def run_integration(args):
         return
     if w == "c3sweep":
         # configuration 3's active-block sweep: N = 2^20 equal masses, eps = 1/4096, the first n of
-        # a seeded shuffle; mixed vs FP64 GPU path rates, and both paths' errors vs the oracle on
-        # 1024 sampled active particles
-        N, eps = 1 << 20, 1.0 / 4096
+        # a seeded shuffle, on a state of the block-step schedule (the initial forces and steps,
+        # each particle's time the last multiple of its step before T = 1/16, so prediction runs
+        # over h up to a whole step).  Per n: the mixed path with the separate predictor of all N
+        # (nb_predict + nb_compute_forces), the same forces with the j-particles predicted on the
+        # fly (nb_compute_forces_at: GRAPE's split, Sec. 4.4 steps 3-4), and the FP64 path; errors
+        # vs the oracle (FP64 prediction of all N, compensated sums) on 1024 sampled particles
+        N, eps, T = 1 << 20, 1.0 / 4096, 2.0 ** -4
         m, x, v = inputs.plummer(N, 3)
+        s = nb.NBody(N, nb.NB_MIXED, 0)
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()
+        st = s.get_particles(0, N)
+        s.close()
+        ti = (np.ceil(T / st["dt"]) - 1.0) * st["dt"]
+        state = (m, x, v, st["a"], st["jerk"], ti, st["dt"])
+        xp, vp = oracle.predict(x, v, st["a"], st["jerk"], ti, T)
         res = []
-        for n in (256, 4096, inputs.block_size(N), 65536, N):
+        for n in (256, 1024, 2048, 4096, 8192, inputs.block_size(N), 65536, N):
             act = inputs.sample_indices(N, n, 1003).astype(np.int32)
             pos = inputs.sample_indices(n, min(n, 1024), 2003)
-            ref = oracle.forces(m, x, v, eps, idx=act[pos].astype(np.int64))
+            ref = oracle.forces(m, xp, vp, eps, idx=act[pos].astype(np.int64), compensated=True)
             row = {"n_active": n}
-            for prec, name in ((nb.NB_MIXED, "mixed"), (nb.NB_FP64, "fp64")):
+            for prec, name in ((nb.NB_MIXED, "mixed"), (nb.NB_MIXED, "mixed_onthefly"), (nb.NB_FP64, "fp64")):
                 if prec == nb.NB_FP64 and n > 65536:
                     continue  # 1.1e12 FP64 interactions take over a minute; the sample covers accuracy
                 s = nb.NBody(N, prec, 0, stream=torch.cuda.current_stream())
                 s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
-                s.set_j_particles(0, m, x, v)
-                s.predict(0.0)
+                s.set_j_particles(0, *state)
                 d_act = torch.from_numpy(act).cuda()
                 A = torch.empty((n, 3), dtype=torch.float64, device="cuda")
                 J = torch.empty_like(A)
                 P = torch.empty(n, dtype=torch.float64, device="cuda")
-                s.compute_forces(d_act, A, J, P)
-                reps = 3 if n * N < 1e11 else 1
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+                def once():
+                    ev[0].record()
+                    if name == "mixed_onthefly":
+                        s.compute_forces_at(T, d_act, A, J, P)
+                        ev[1].record()
+                    else:
+                        s.predict(T)
+                        ev[1].record()
+                        s.compute_forces(d_act, A, J, P)
+                    ev[2].record()
+
+                once()  # warm-up (the first on-the-fly call also builds the j-memory)
+                reps = 5 if n * N < 1e10 else (3 if n * N < 1e11 else 1)
+                tp, tf = [], []
                 for _ in range(reps):
-                    s.compute_forces(d_act, A, J, P)
-                e1.record()
-                torch.cuda.synchronize()
-                sec = e0.elapsed_time(e1) / 1e3 / reps
+                    once()
+                    torch.cuda.synchronize()
+                    tp.append(ev[0].elapsed_time(ev[1]))
+                    tf.append(ev[1].elapsed_time(ev[2]))
+                tp, tf = float(np.median(tp)), float(np.median(tf))
                 pp = torch.from_numpy(pos).cuda()
                 a, j, p = A[pp].cpu().numpy(), J[pp].cpu().numpy(), P[pp].cpu().numpy()
                 s.close()
                 ea, ej, ep = rel(a, ref[0]), rel(j, ref[1]), np.abs(p - ref[2]) / np.abs(ref[2])
-                row[name] = {"ms": sec * 1e3, "interactions_per_s": float(n) * N / sec,
-                             "frac_fp32_peak_60flop": float(n) * N / sec * 60 / 80.548e12,
+                tot = tp + tf
+                if name == "mixed_onthefly":  # one call: list prediction, boxes and forces
+                    tp, tf = None, tot
+                row[name] = {"ms_predict": tp, "ms_force": tf, "ms_total": tot,
+                             "interactions_per_s": float(n) * N / (tot / 1e3),
+                             "frac_fp32_peak_60flop_force": float(n) * N / (tf / 1e3) * 60 / 80.548e12,
                              "acc_median": float(np.median(ea)), "acc_max": float(ea.max()),
                              "jerk_median": float(np.median(ej)), "jerk_max": float(ej.max()),
                              "pot_max": float(ep.max())}
+            row["onthefly_speedup"] = row["mixed"]["ms_total"] / row["mixed_onthefly"]["ms_total"]
             res.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
-        print(json.dumps({"workload": "c3sweep", "N": N, "eps": eps, "rows": res}), flush=True)
+        print(json.dumps({"workload": "c3sweep", "N": N, "eps": eps, "T": T, "rows": res}), flush=True)
         return
     if w == "tapp":
         # T_app for one N-body time unit vs N on one GB300 (the single-node curves of the paper's
@@ -487,7 +531,23 @@ def run_integration(args):
             tim = s.get_timings()
             c1 = s.get_counters()
             k1, w1 = s.energy()
+            jp = s.get_jpredict()
             s.close()
+            # the host loop again with every block predicting all N first (the on-the-fly j
+            # prediction of small blocks, Sec. 4.4 steps 3-4, switched off): the ablation
+            h2 = nb.NBody(N, nb.NB_MIXED, 0)
+            h2.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
+            h2.set_j_particles(0, m, x, v)
+            h2.initial_forces_and_dt()
+            h2.set_jpredict(0)
+            ch0 = h2.get_counters()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2.integrate(1.0, use_graph=False)
+            torch.cuda.synchronize()
+            wall_sep = time.perf_counter() - t0
+            steps_sep = h2.get_counters()["block_steps"] - ch0["block_steps"]
+            h2.close()
             # the same time unit with the whole block-step loop on the device (one CUDA graph)
             g = nb.NBody(N, nb.NB_MIXED, 0)
             g.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
@@ -521,17 +581,29 @@ def run_integration(args):
             inter = tim["interactions"]
             psteps = inter / N
             tp, tf, tc = tim["ms_pred"] / 1e3, tim["ms_force"] / 1e3, tim["ms_corr"] / 1e3
+            taus = sec41_taus(tp, tf, tc, N, steps, inter, psteps)
             out.append({"N": N, "profile_step": {"n": n, "ms_predict": pr[0], "ms_force": pr[1], "ms_correct": pr[2]},
                         "T_app_s": wall, "block_steps": steps, "particle_steps": psteps, "interactions": inter,
                         "interactions_per_s": inter / wall,
-                        "tau_pred_s": tp / (steps * N), "tau_force_s": tf / inter, "tau_corr_s": tc / psteps,
-                        "model_T_s": tp + tf + tc, "share_force": tf / wall, "share_pred": tp / wall,
+                        "tau_pred_s": taus[0], "tau_force_s": taus[1], "tau_corr_s": taus[2],
+                        "model_T_s": sec41_T(taus, N, steps, inter, psteps), "share_force": tf / wall,
+                        "share_pred": tp / wall,
                         "share_corr": tc / wall, "share_host_and_select": 1 - (tp + tf + tc) / wall,
                         "energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0),
+                        "jpredict_max_n": jp,
+                        "T_app_host_separate_predictor_s": wall_sep, "block_steps_separate": steps_sep,
                         "T_app_graph_s": wall_g, "energy_drift_graph": abs((kg + wg) - (k0 + w0)) / abs(k0 + w0),
                         "T_app_persistent_s": wall_p, "block_steps_persistent": steps_p,
                         "energy_drift_persistent": drift_p})
             print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+        # the paper calibrates its model on one run (N = 32768, Sec. 4.1) and predicts the others:
+        # the same with the tau's of the N = 32768 row (when it was run)
+        cal = [r for r in out if r["N"] == 32768]
+        if cal:
+            taus = (cal[0]["tau_pred_s"], cal[0]["tau_force_s"], cal[0]["tau_corr_s"])
+            for r in out:
+                r["model_T_calibrated_at_32768_s"] = sec41_T(taus, r["N"], r["block_steps"], r["interactions"],
+                                                             r["particle_steps"])
         print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": "mixed",
                           "grape_tau_force_s": 4.3e-10, "rows": out}), flush=True)
         return

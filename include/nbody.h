@@ -164,8 +164,48 @@ int nb_compute_forces(nb_ctx* ctx, const int32_t* i_idx, int64_t n, double* acc,
                       double* pot, int ptr_kind);
 
 /*
+ * nb_compute_forces_at -- GRAPE's split of steps 3-5 (Sec. 4.4 steps 3-5):
+ * the n listed particles i_idx (ascending, unique, < N) are predicted to t
+ * alone (step 3, in FP64 as nb_predict does), every j-particle is predicted
+ * to t inside the force kernel as its tile is loaded (step 4, the board's
+ * on-the-fly prediction), and the forces on the list are summed as in
+ * nb_compute_forces (step 5).  No nb_predict of all N is needed; t must lie
+ * within every particle's current step (t_j <= t <= t_j + dt_j, as any block
+ * time of the particles' schedule does).  Outputs and errors as
+ * nb_compute_forces; the results are kept for nb_correct(t).
+ *
+ * Mixed path: the kernel predicts from a "j-memory" of double-single records
+ * (80 bytes per particle, allocated on the first call and kept current
+ * through the context's own corrections): x + v h is carried in
+ * double-single FP32 (~2^-48), the acceleration and jerk terms in FP32
+ * (error <= 2^-24 |a| h^2/2 + ...), velocities in FP32.  NB_FP64: there is
+ * no on-the-fly prediction; all N are predicted first (as nb_predict).
+ */
+int nb_compute_forces_at(nb_ctx* ctx, double t, const int32_t* i_idx, int64_t n, double* acc, double* jerk,
+                         double* pot, int ptr_kind);
+
+/*
+ * nb_set_jpredict -- which block steps of the host-driven loop (nb_step,
+ * nb_integrate with NB_LOOP_HOST) take the on-the-fly j prediction of
+ * nb_compute_forces_at instead of predicting all N first (mixed path, single
+ * system): blocks of n <= max_n active particles.  max_n = 0 never,
+ * NB_JPREDICT_AUTO (the default) the measured crossover on GB300, n <= 1024
+ * (the in-kernel prediction costs ~5% of the force kernel, the separate
+ * predictor of all N a fixed pass over the state).  The block steps are the
+ * same; the predicted j differ from the FP64 predictor's in the last bits
+ * (see nb_compute_forces_at).  The j-memory is allocated on the first block
+ * that takes this path.  Errors: NB_EINVAL (max_n < -1).
+ */
+#define NB_JPREDICT_AUTO (-1)
+int nb_set_jpredict(nb_ctx* ctx, int64_t max_n);
+
+/* nb_get_jpredict -- the largest block that takes the on-the-fly prediction. */
+int nb_get_jpredict(nb_ctx* ctx, int64_t* max_n);
+
+/*
  * nb_correct -- Sec. 4.1 step 5: 4th-order Hermite correction of the n
- * particles i_idx (the list of the preceding nb_compute_forces) to time t,
+ * particles i_idx (the list of the preceding nb_compute_forces or
+ * nb_compute_forces_at(t)) to time t,
  * using their old (a, jerk) and the new ones; stores the new a, jerk, pot,
  * t_i = t and a new block step dt_i: the Aarseth criterion with eta,
  * rounded down to a power of two, clamped to [dt_min, dt_max], growing at

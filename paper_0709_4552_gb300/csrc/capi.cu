@@ -17,6 +17,12 @@ constexpr double kDefaultEta = 0.01;
 constexpr double kDefaultDtMin = 1.0 / 4194304.0;  // Sec. 2: 2^-22
 constexpr double kDefaultDtMax = 0.125;            // Sec. 2: 2^-3
 constexpr size_t kPinnedBytes = 1 << 16;
+// largest block the on-the-fly j prediction takes under NB_JPREDICT_AUTO (the
+// default): measured on a GB300 at N = 2^20, the in-kernel prediction costs
+// ~5% of the force kernel at every block size, the separate predictor of all
+// N a fixed ~0.095 ms, so the split wins below n ~ 1000 (n = 256: 1.13x of
+// predict + forces; n = 1024: even; n = 4096: 0.96x)
+constexpr int64_t kJpredictAutoMaxN = 1024;
 
 int fail(nb_ctx* c, int code) {
   if (c && c->last_error == NB_OK && code != NB_OK) c->last_error = code;
@@ -62,7 +68,7 @@ void free_ctx(nb_ctx* c) {
   void* dptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->jA, c->jB,
                    c->jC, c->F, c->part, c->act, c->ident, c->ulist, c->sel_min, c->sel_cnt, c->red,
                    c->status, c->d_offsets, c->d_ceps, c->perm, c->iperm, c->skey[0], c->skey[1],
-                   c->sval[0], c->sval[1], c->shist, c->tbox, c->mlist, c->pscratch};
+                   c->sval[0], c->sval[1], c->shist, c->tbox, c->mlist, c->pscratch, c->jm};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -192,6 +198,7 @@ int ensure_sorted(nb_ctx* c) {
   if (c->n <= 0 || c->precision != NB_MIXED) return NB_OK;
   if (c->perm_valid && c->perm_age < c->sort_interval) return NB_OK;
   NB_CUDA(c, nb_spatial_sort(c));
+  c->state_ver++;  // rows moved
   c->perm_valid = true;
   c->perm_age = 0;
   c->pred_valid = false;
@@ -237,14 +244,56 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+// blocks that take the on-the-fly j prediction (mixed single system)
+bool use_jpredict(const nb_ctx* c, int64_t n) {
+  return c->precision == NB_MIXED && c->n_clusters == 0 && n > 0 && n <= c->jpred_max_n;
+}
+
+// host side of the on-the-fly split: the list predicted to t and the far-test
+// boxes of the j-memory tiles (null when the pass is off), one launch
+int jm_host_side(nb_ctx* c, const int32_t* d_list, int64_t n, double t, const float4** boxes) {
+  const bool b = c->perm_valid && c->far_tiles;
+  NB_CUDA(c, nb_launch_jm_host_side(c, d_list, n, t, b));
+  *boxes = b ? c->tbox : nullptr;
+  return NB_OK;
+}
+
+// a correction of the rows d_list that keeps a current j-memory current (the
+// corrector writes the corrected records), then counts the change of state
+int correct_rows(nb_ctx* c, const int32_t* d_list, int64_t n, double t) {
+  const bool keep = c->jm && c->jm_ver == c->state_ver;
+  NB_CUDA(c, nb_launch_correct(c, d_list, n, t, keep));
+  c->state_ver++;
+  if (keep) c->jm_ver = c->state_ver;
+  return NB_OK;
+}
+
 // one block step after selection (t_next, n known): predict, forces, correct
+// (Sec. 4.1 steps 3-5); small blocks may take GRAPE's split instead (Sec. 4.4
+// steps 3-7: the active particles predicted alone, the j on the fly)
 int step_after_select(nb_ctx* c, double t, int64_t n) {
+  const bool fused = use_jpredict(c, n);
+  if (fused) {
+    const int r = nb_jm_ensure(c);
+    if (r) return fail(c, r);
+  }
   NB_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
-  NB_CUDA(c, nb_launch_predict(c, t, false));
-  NB_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
-  NB_CUDA(c, nb_forces(c, c->act, n));
+  if (fused) {
+    const float4* boxes = nullptr;
+    int r = jm_host_side(c, c->act, n, t, &boxes);
+    if (r) return r;
+    NB_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    NB_CUDA(c, nb_forces_mixed_fused(c, c->act, n, pick_tuning(c, n), nullptr, t, boxes));
+  } else {
+    NB_CUDA(c, nb_launch_predict(c, t, false));
+    NB_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    NB_CUDA(c, nb_forces(c, c->act, n));
+  }
   NB_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-  NB_CUDA(c, nb_launch_correct(c, c->act, n, t));
+  {
+    const int r = correct_rows(c, c->act, n, t);
+    if (r) return r;
+  }
   NB_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   c->interactions += (double)n * (double)c->n;
   c->pred_valid = false;
@@ -272,6 +321,20 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
   if (st.flags & NB_ST_TIMEOUT) return NB_ETIMEOUT;
   if (st.flags & NB_ST_NUMERIC) return NB_ENUMERIC;
   if (st.flags & NB_ST_BADLIST) return NB_EINVAL;
+  return NB_OK;
+}
+
+// the force rows of the last call to the caller (host copies complete on return)
+int copy_forces_out(nb_ctx* c, int64_t n, double* acc, double* jerk, double* pot, int ptr_kind) {
+  int r;
+  for (int q = 0; q < 2; ++q) {
+    double* dst = q == 0 ? acc : jerk;
+    if (!dst) continue;
+    if ((r = get_vec(c, c->F + 3 * q * c->n_pad, c->n_pad, dst, n, ptr_kind))) return r;
+    if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  if ((r = get_scalar(c, c->F + 6 * c->n_pad, pot, n, ptr_kind))) return r;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
   return NB_OK;
 }
 
@@ -341,6 +404,8 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
   c->sel_ctas = 1024;
   c->sort_interval = 64;
   c->far_tiles = 1;
+  c->jm_ver = -1;
+  c->jpred_max_n = kJpredictAutoMaxN;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = sms > 0 ? sms : 1;
@@ -457,6 +522,8 @@ int nb_set_j_particles(nb_ctx* c, int64_t first, int64_t count, const double* m,
   c->perm_valid = false;
   c->pred_valid = false;
   c->f_valid = false;
+  c->plist_valid = false;
+  c->state_ver++;
   return NB_OK;
 }
 
@@ -468,7 +535,9 @@ int nb_set_n(nb_ctx* c, int64_t n) {
   c->n = n;
   c->pred_valid = false;
   c->f_valid = false;
+  c->plist_valid = false;
   c->perm_valid = false;
+  c->state_ver++;
   return NB_OK;
 }
 
@@ -521,6 +590,7 @@ int nb_predict(nb_ctx* c, double t) {
   NB_CUDA(c, nb_launch_predict(c, t, false));
   c->t_pred = t;
   c->pred_valid = true;
+  c->plist_valid = false;
   return NB_OK;
 }
 
@@ -540,18 +610,64 @@ int nb_compute_forces(nb_ctx* c, const int32_t* i_idx, int64_t n, double* acc, d
   c->f_n = n;
   c->f_valid = true;
   c->f_list = d_list;
+  c->plist_valid = false;
   c->interactions += (double)n * (double)c->n;
-  for (int q = 0; q < 2; ++q) {
-    double* dst = q == 0 ? acc : jerk;
-    if (!dst) continue;
-    if ((r = get_vec(c, c->F + 3 * q * c->n_pad, c->n_pad, dst, n, ptr_kind))) return r;
-    if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  r = copy_forces_out(c, n, acc, jerk, pot, ptr_kind);
+  if (r) return r;
+  if (ptr_kind == NB_PTR_HOST) c->ms_force += elapsed(c->ev[4], c->ev[5]);
+  return NB_OK;
+}
+
+int nb_compute_forces_at(nb_ctx* c, double t, const int32_t* i_idx, int64_t n, double* acc, double* jerk,
+                         double* pot, int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n || (n > 0 && !i_idx) || !isfinite(t)) return fail(c, NB_EINVAL);
+  if (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE) return fail(c, NB_EINVAL);
+  if (c->n <= 0) return fail(c, NB_ESTATE);
+  if (n == 0) return NB_OK;
+  int r = ensure_sorted(c);
+  if (r) return r;
+  const int32_t* d_list = nullptr;
+  if ((r = caller_list(c, i_idx, n, ptr_kind, &d_list))) return r;
+  NB_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
+  if (c->precision == NB_MIXED) {
+    if ((r = nb_jm_ensure(c))) return fail(c, r);
+    const float4* boxes = nullptr;
+    if ((r = jm_host_side(c, d_list, n, t, &boxes))) return r;
+    const int32_t* ord = nullptr;
+    if (c->perm_valid && n >= 2048) NB_CUDA(c, nb_list_order(c, d_list, n, &ord));
+    NB_CUDA(c, nb_forces_mixed_fused(c, d_list, n, pick_tuning(c, n), ord, t, boxes));
+  } else {
+    // the FP64 path predicts every particle (it has no on-the-fly prediction)
+    NB_CUDA(c, nb_launch_predict(c, t, false));
+    NB_CUDA(c, nb_forces(c, d_list, n));
   }
-  if ((r = get_scalar(c, c->F + 6 * c->n_pad, pot, n, ptr_kind))) return r;
-  if (ptr_kind == NB_PTR_HOST) {
-    NB_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->ms_force += elapsed(c->ev[4], c->ev[5]);
-  }
+  NB_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
+  // the listed rows now hold their prediction at t, the others an older one
+  c->pred_valid = c->precision == NB_FP64;
+  c->t_pred = t;
+  c->f_n = n;
+  c->f_valid = true;
+  c->f_list = d_list;
+  c->plist_valid = true;
+  c->t_plist = t;
+  c->interactions += (double)n * (double)c->n;
+  r = copy_forces_out(c, n, acc, jerk, pot, ptr_kind);
+  if (r) return r;
+  if (ptr_kind == NB_PTR_HOST) c->ms_force += elapsed(c->ev[4], c->ev[5]);
+  return NB_OK;
+}
+
+int nb_set_jpredict(nb_ctx* c, int64_t max_n) {
+  if (!c) return NB_EINVAL;
+  if (max_n < NB_JPREDICT_AUTO) return fail(c, NB_EINVAL);
+  c->jpred_max_n = max_n == NB_JPREDICT_AUTO ? kJpredictAutoMaxN : max_n;
+  return NB_OK;
+}
+
+int nb_get_jpredict(nb_ctx* c, int64_t* max_n) {
+  if (!c || !max_n) return NB_EINVAL;
+  *max_n = c->jpred_max_n;
   return NB_OK;
 }
 
@@ -559,13 +675,17 @@ int nb_correct(nb_ctx* c, const int32_t* i_idx, int64_t n, double t, int ptr_kin
   NB_SINGLE(c);
   if (n < 0 || n > c->n || (n > 0 && !i_idx) || !isfinite(t)) return fail(c, NB_EINVAL);
   if (n == 0) return NB_OK;
-  if (!c->f_valid || c->f_n != n || !c->pred_valid) return fail(c, NB_ESTATE);
+  // the listed particles must be predicted to t: by nb_predict, or by the
+  // list prediction of nb_compute_forces_at
+  const bool predicted = c->pred_valid || (c->plist_valid && t == c->t_plist);
+  if (!c->f_valid || c->f_n != n || !predicted) return fail(c, NB_ESTATE);
   const int32_t* d_list = nullptr;
   int r = caller_list(c, i_idx, n, ptr_kind, &d_list);
   if (r) return r;
-  NB_CUDA(c, nb_launch_correct(c, d_list, n, t));
+  if ((r = correct_rows(c, d_list, n, t))) return r;
   c->f_valid = false;
   c->pred_valid = false;
+  c->plist_valid = false;
   if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
   return NB_OK;
 }
@@ -587,6 +707,8 @@ int nb_initial_forces_and_dt(nb_ctx* c) {
   c->interactions += (double)c->n * (double)c->n;
   c->pred_valid = false;
   c->f_valid = false;
+  c->plist_valid = false;
+  c->state_ver++;
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   return device_status_code(c, nullptr) == NB_ENUMERIC ? fail(c, NB_ENUMERIC) : NB_OK;
 }
@@ -634,6 +756,8 @@ int nb_integrate(nb_ctx* c, double t_end, int loop) {
   int r = loop == NB_LOOP_GRAPH        ? nb_integrate_graph(c, t_end)
           : loop == NB_LOOP_PERSISTENT ? nb_integrate_persistent(c, t_end)
                                        : integrate_host_loop(c, t_end);
+  if (loop != NB_LOOP_HOST) c->state_ver++;  // device-driven corrections (the host loop counts its own)
+  c->plist_valid = false;
   if (r) return fail(c, r);
   r = device_status_code(c, nullptr);
   if (r == NB_ENUMERIC || r == NB_ETIMEOUT) return fail(c, r);
@@ -658,6 +782,7 @@ int nb_energy(nb_ctx* c, double* ekin, double* epot) {
   if (ekin) *ekin = h[0];
   if (epot) *epot = h[1];
   c->pred_valid = false;
+  c->plist_valid = false;
   c->f_valid = false;
   return NB_OK;
 }

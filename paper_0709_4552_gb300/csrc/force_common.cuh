@@ -91,9 +91,45 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <int JT>
 struct MixedSmem {
+  static constexpr bool kFused = false;
   float4 A[2][JT];
   float4 B[2][JT];
   float2 C[2][JT];
+};
+
+// ---- on-the-fly prediction of the j-particles (Sec. 4.4 step 4) -------------
+// GRAPE predicts the j-particles on the board, in its pipelines, as they
+// stream past; the host predicts only the n active i (step 3).  Here the
+// force item can do the same: instead of a predicted j-store it loads the
+// "j-memory" record of each particle, written from its FP64 state after every
+// correction (rows in the resident order, 5 float4 rows of stride n_pad):
+//   R0 = (xh, m)   R1 = (xl, Rd)   R2 = (vh, j6.x)   R3 = (vl, j6.y)   R4 = (a2, j6.z)
+// with x = xh + xl and v = vh + vl the double-single splits of the FP64
+// position and velocity, a2 = fl32(a/2), j6 = fl32(jerk/6), and Rd a bound
+// on the distance the particle can move within its current step (the tile
+// boxes of the far test are grown by it), plus its FP64 time t_j.  The item
+// predicts the tile it has staged, to the block time T, into the same
+// pair-interleaved shared tile the plain loader fills:
+//   h = fl32(T - t_j)  (exact: a multiple of dt_min below dt_max),
+//   xp = x + h (v + h (a/2 + h j/6))  in double-single FP32 (TwoSum and an
+//        FMA-exact product carry the x + v h part to ~2^-48; the a and jerk
+//        terms are FP32, so their rounding is 2^-24 |a h^2 / 2| at most),
+//   vp = v + h (a + h j/2)  in FP32 (the mixed path's velocities are FP32).
+template <int JT>
+struct FusedSmem {
+  static constexpr bool kFused = true;
+  float4 R[2][5][JT];  // staged j-memory records (double-buffered)
+  double T[2][JT];     // their times t_j
+  float4 A[JT];        // the predicted tile, pair-interleaved (PairTile)
+  float4 B[JT];
+  float2 C[JT];
+};
+
+struct FusedArgs {
+  const float4* __restrict__ jm = nullptr;  // R0..R4 rows, stride n_pad
+  int64_t stride = 0;
+  const double* __restrict__ tj = nullptr;  // FP64 times of the rows
+  double T = 0.0;                           // block time
 };
 
 template <int NT, int JT>
@@ -148,6 +184,110 @@ __device__ __forceinline__ void mixed_load_tile_pairs(float4* sA, float4* sB, fl
     cp_async4(t.p4 + o, b + 1);
     cp_async4(t.p4 + o + 2, b + 2);
   }
+}
+
+template <int NT, int JT>
+__device__ __forceinline__ void jm_load_tile(FusedSmem<JT>& sm, int buf, const FusedArgs& fa, int64_t j0,
+                                             int64_t jhi) {
+#pragma unroll
+  for (int q = threadIdx.x; q < JT; q += NT) {
+    const int64_t j = min(j0 + q, jhi - 1);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) cp_async16(&sm.R[buf][k][q], &fa.jm[k * fa.stride + j]);
+    cp_async8(&sm.T[buf][q], &fa.tj[j]);
+  }
+}
+
+// x + delta in double-single: (xh, xl) + (p + q) with p + q = h (s + e) exact
+// up to the rounding of e; TwoSum keeps the rounding error of xh + p.  The
+// velocity: v + h (a + h j/2) = vh + 2h (a/2 + (3h/2) j/6) in FP32.  F2 is
+// float (one coordinate) or float2 (two coordinates in the packed FP32x2
+// operations, each lane rounded exactly as the scalar form).
+__device__ __forceinline__ float p_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float p_sub(float a, float b) { return a - b; }
+__device__ __forceinline__ float p_mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float p_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float p_neg(float a) { return -a; }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <typename F2>
+__device__ __forceinline__ void ds_predict(F2 xh, F2 xl, F2 vh, F2 vl, F2 a2, F2 j6, F2 h, F2 h2, F2 h15,
+                                           F2& hi, F2& lo, F2& vp) {
+  const F2 u = p_fma(h, j6, a2);  // a/2 + h j/6
+  const F2 hu = p_mul(h, u);
+  F2 s = p_add(vh, hu);  // TwoSum(vh, hu)
+  F2 bb = p_sub(s, vh);
+  F2 e = p_add(p_sub(vh, p_sub(s, bb)), p_sub(hu, bb));
+  e = p_add(e, vl);
+  const F2 p = p_mul(h, s);  // h (s + e) = p + q, the product h s exact (FMA)
+  F2 q = p_fma(h, s, p_neg(p));
+  q = p_fma(h, e, q);
+  const F2 S = p_add(xh, p);  // TwoSum(xh, p)
+  bb = p_sub(S, xh);
+  F2 E = p_add(p_sub(xh, p_sub(S, bb)), p_sub(p, bb));
+  E = p_add(E, p_add(xl, q));
+  hi = p_add(S, E);  // renormalise: |lo| <= ulp(hi) / 2
+  lo = p_sub(E, p_sub(hi, S));
+  vp = p_fma(h2, p_fma(h15, j6, a2), vh);
+}
+
+// predict the staged tile `buf` into the pair tile; slots past jhi become
+// massless particles far away (every float written, so no stale shared
+// memory is ever read)
+template <int NT, int JT>
+__device__ __forceinline__ void jm_predict_tile(FusedSmem<JT>& sm, int buf, double T, int64_t jt, int64_t jhi) {
+  const PairTile<JT> pt(sm.A, sm.B, sm.C);
+#pragma unroll
+  for (int q = threadIdx.x; q < JT; q += NT) {
+    const int o = 4 * (q >> 1) + (q & 1);
+    float xh[3], xl[3], vv[3], m;
+    if (jt + q < jhi) {
+      const float4 r0 = sm.R[buf][0][q], r1 = sm.R[buf][1][q], r2 = sm.R[buf][2][q], r3 = sm.R[buf][3][q],
+                   r4 = sm.R[buf][4][q];
+      const float h = __double2float_rn(T - sm.T[buf][q]);
+      const float h2 = 2.0f * h, h15 = 1.5f * h;  // exact scalings of an exact h
+      float2 hi2, lo2, vp2;
+      ds_predict(make_float2(r0.x, r0.y), make_float2(r1.x, r1.y), make_float2(r2.x, r2.y),
+                 make_float2(r3.x, r3.y), make_float2(r4.x, r4.y), make_float2(r2.w, r3.w), make_float2(h, h),
+                 make_float2(h2, h2), make_float2(h15, h15), hi2, lo2, vp2);
+      ds_predict(r0.z, r1.z, r2.z, r3.z, r4.z, r4.w, h, h2, h15, xh[2], xl[2], vv[2]);
+      xh[0] = hi2.x; xh[1] = hi2.y;
+      xl[0] = lo2.x; xl[1] = lo2.y;
+      vv[0] = vp2.x; vv[1] = vp2.y;
+      m = r0.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xh[c] = kFarF;
+        xl[c] = 0.0f;
+        vv[c] = 0.0f;
+      }
+      m = 0.0f;
+    }
+    pt.p0[o] = xh[0];
+    pt.p0[o + 2] = xh[1];
+    pt.p1[o] = xh[2];
+    pt.p1[o + 2] = m;
+    pt.p2[o] = vv[0];
+    pt.p2[o + 2] = vv[1];
+    pt.p3[o] = vv[2];
+    pt.p3[o + 2] = xl[0];
+    pt.p4[o] = xl[1];
+    pt.p4[o + 2] = xl[2];
+  }
+}
+
+template <int JT>
+__device__ __forceinline__ PairTile<JT> pair_tile(MixedSmem<JT>& sm, int buf) {
+  return PairTile<JT>(sm.A[buf], sm.B[buf], sm.C[buf]);
+}
+template <int JT>
+__device__ __forceinline__ PairTile<JT> pair_tile(FusedSmem<JT>& sm, int) {
+  return PairTile<JT>(sm.A, sm.B, sm.C);
 }
 
 // One j-tile against the thread's IPT i-particles; FP32 partials in p.
@@ -275,14 +415,18 @@ __device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const flo
 // Mixed-precision item: i-tile starting at list position ibase (n entries in
 // list, entries clamped to [0, idx_hi)), j-range [jlo, jhi).  Writes 7 rows
 // out[c * ostride + pos] (final: acc, jerk, pot with its sign) or raw sums.
-template <int NT, int IPT, int JT>
-__device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __restrict__ jA,
+// With FusedSmem the j-tiles come from the j-memory (fa) and are predicted
+// to fa.T as they are staged; the i-particles always come from jA/jB/jC.
+template <int NT, int IPT, int JT, typename SM>
+__device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA,
                                            const float4* __restrict__ jB, const float2* __restrict__ jC,
                                            int64_t jlo, int64_t jhi, int64_t idx_hi,
                                            const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                            float eps2, double* __restrict__ out, int64_t ostride,
                                            bool finalize, const float4* __restrict__ tbox = nullptr,
-                                           const int32_t* __restrict__ ord = nullptr, int64_t box_origin = 0) {
+                                           const int32_t* __restrict__ ord = nullptr, int64_t box_origin = 0,
+                                           const FusedArgs fa = FusedArgs()) {
+  constexpr bool kFusedLoad = SM::kFused;
   // list: j-store slots of the i-particles.  ord (optional): the list
   // positions in processing order (a caller's list visited in spatial
   // order); results always go to the list positions.  tbox (optional):
@@ -361,6 +505,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 
   // packed loop: each i-particle in both lanes, negated
   constexpr bool kPk = NB_MIXED_PACKED && IPT <= 2;
+  static_assert(!kFusedLoad || kPk, "on-the-fly prediction fills the pair layout of the packed loop");
   float2 nxh[IPT][3], nxl[IPT][3], nv[IPT][3];
 #pragma unroll
   for (int k = 0; k < IPT; ++k)
@@ -373,7 +518,9 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
 
   const int ntiles = (int)((jhi - jlo + JT - 1) / JT);
   if (ntiles > 0) {
-    if constexpr (kPk)
+    if constexpr (kFusedLoad)
+      jm_load_tile<NT, JT>(sm, 0, fa, jlo, jhi);
+    else if constexpr (kPk)
       mixed_load_tile_pairs<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
     else
       mixed_load_tile<NT, JT>(sm.A[0], sm.B[0], sm.C[0], jA, jB, jC, jlo, jhi);
@@ -384,7 +531,9 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     const int buf = tile & 1;
     const int64_t jt = jlo + (int64_t)tile * JT;
     if (tile + 1 < ntiles) {
-      if constexpr (kPk)
+      if constexpr (kFusedLoad)
+        jm_load_tile<NT, JT>(sm, buf ^ 1, fa, jt + JT, jhi);
+      else if constexpr (kPk)
         mixed_load_tile_pairs<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
       else
         mixed_load_tile<NT, JT>(sm.A[buf ^ 1], sm.B[buf ^ 1], sm.C[buf ^ 1], jA, jB, jC, jt + JT, jhi);
@@ -392,7 +541,11 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    if (jt + JT > jhi) {  // ragged last tile: massless far-away particles past jhi
+    if constexpr (kFusedLoad) {
+      // predict the staged tile (ragged tail included) into the pair tile
+      jm_predict_tile<NT, JT>(sm, buf, fa.T, jt, jhi);
+      __syncthreads();
+    } else if (jt + JT > jhi) {  // ragged last tile: massless far-away particles past jhi
       for (int q = tid; q < JT; q += NT) {
         if (jt + q < jhi) continue;
         if constexpr (kPk) {
@@ -443,7 +596,7 @@ __device__ __forceinline__ void mixed_item(MixedSmem<JT>& sm, const float4* __re
       }
     }
     if constexpr (kPk) {
-      const PairTile<JT> pt(sm.A[buf], sm.B[buf], sm.C[buf]);
+      const PairTile<JT> pt = pair_tile(sm, buf);
       const float2 e2 = make_float2(eps2, eps2);
       float2 p2[IPT][7];
 #pragma unroll

@@ -35,6 +35,29 @@ __global__ void NB_MIXED_BOUNDS(NT, IPT) force_mixed_kernel(
                                eps2, o, ostride, finalize != 0, tbox, ord);
 }
 
+// the same item with on-the-fly prediction of the j-tiles from the j-memory
+// (Sec. 4.4 step 4); the i-particles' predicted rows are in jA/jB/jC
+template <int NT, int JT>
+__global__ void __launch_bounds__(NT) force_mixed_fused_kernel(
+    const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
+    int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t tiles, float eps2,
+    double* __restrict__ out, int64_t ostride, int finalize, const float4* __restrict__ tbox,
+    const int32_t* __restrict__ ord, const float4* __restrict__ jm, int64_t jm_stride,
+    const double* __restrict__ tj, double T) {
+  __shared__ __align__(16) nbk::FusedSmem<JT> sm;
+  const int split = blockIdx.y;
+  const int64_t jlo = nbk::split_begin(split, gridDim.y, tiles) * JT;
+  const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
+  double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
+  nbk::FusedArgs fa;
+  fa.jm = jm;
+  fa.stride = jm_stride;
+  fa.tj = tj;
+  fa.T = T;
+  nbk::mixed_item<NT, 1, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * NT, eps2, o, ostride,
+                             finalize != 0, tbox, ord, 0, fa);
+}
+
 template <int NT, int IPT, int JT>
 cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg, float eps2,
                    const int32_t* ord) {
@@ -66,6 +89,38 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
 }
 
 }  // namespace
+
+// forces on d_list with the j-tiles predicted to T on the fly (default launch
+// shape: 128 threads, one i per thread, 128-particle j-tiles); boxes, when
+// given, are the j-memory tile boxes grown by each particle's reach
+cudaError_t nb_forces_mixed_fused(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                                  const int32_t* ord, double T, const float4* boxes) {
+  constexpr int NT = 128, JT = 128;
+  if (n <= 0) return cudaSuccess;
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_mixed_fused_kernel<NT, JT>, NT, 0) != cudaSuccess)
+    return cudaGetLastError();
+  const nb_tuning shape{1, NT, JT, cfg.nsplit};
+  int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, shape, per_sm);
+  const int64_t itiles = (n + NT - 1) / NT;
+  const int64_t n_j = ((c->n + JT - 1) / JT) * JT;
+  const int64_t tiles = n_j / JT;
+  if (nsplit > tiles) nsplit = (int)tiles;
+  if (nsplit < 1) nsplit = 1;
+  const bool fin = nsplit == 1;
+  const int64_t ostride = fin ? c->n_pad : ((n + 31) / 32) * 32;
+  double* out = fin ? c->F : c->part;
+  if (!fin && (int64_t)nsplit * 7 * ostride > c->part_elems) return cudaErrorInvalidValue;
+  c->launches += fin ? 1 : 2;
+  const float eps2 = (float)(c->eps * c->eps);
+  force_mixed_fused_kernel<NT, JT><<<dim3((unsigned)itiles, (unsigned)nsplit), NT, 0, c->stream>>>(
+      c->jA, c->jB, c->jC, n_j, d_list, n, tiles, eps2, out, ostride, fin ? 1 : 0, boxes, ord, c->jm, c->n_pad,
+      c->t, T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || fin) return e;
+  return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
+}
 
 bool nb_mixed_supported(const nb_tuning& t) {
   const bool thr = t.threads == 64 || t.threads == 128 || t.threads == 256;

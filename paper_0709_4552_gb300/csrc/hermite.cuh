@@ -144,4 +144,48 @@ __device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, 
   dt[i] = dnew;
 }
 
+// j-memory record of row i (the on-the-fly j prediction's input, Sec. 4.4
+// step 4; layout in force_common.cuh): double-single position and velocity,
+// a/2 and jerk/6 in FP32, the mass, and the reach Rd >= |v_c| dt + |a_c| dt^2/2
+// + |j_c| dt^3/6 summed over components (a bound on every coordinate's move
+// within the row's current step), rounded up.  Rows >= N: padding.
+__device__ __forceinline__ void write_jm_record(int64_t i, int64_t N, int64_t n_pad, const double* __restrict__ m,
+                                                const double* __restrict__ x, const double* __restrict__ v,
+                                                const double* __restrict__ a, const double* __restrict__ jk,
+                                                const double* __restrict__ dt, float4* __restrict__ jm) {
+  float xh[3], xl[3], vh[3], vl[3], a2[3], j6[3], mf = 0.0f, reach = 0.0f;
+  if (i < N) {
+    double sv = 0.0, sa = 0.0, sj = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t q = c * n_pad + i;
+      const double xv = x[q], vv = v[q], av = a[q], jv = jk[q];
+      xh[c] = __double2float_rn(xv);
+      xl[c] = __double2float_rn(xv - (double)xh[c]);
+      vh[c] = __double2float_rn(vv);
+      vl[c] = __double2float_rn(vv - (double)vh[c]);
+      a2[c] = __double2float_rn(0.5 * av);
+      j6[c] = __double2float_rn(jv * (1.0 / 6.0));
+      sv += fabs(vv);
+      sa += fabs(av);
+      sj += fabs(jv);
+    }
+    const double d = dt[i];
+    const double r = d * (sv + d * (0.5 * sa + d * (sj * (1.0 / 6.0))));
+    reach = __double2float_ru(r * (1.0 + 0x1p-20));
+    mf = __double2float_rn(m[i]);
+  } else {  // padding row: massless and far away
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xh[c] = (float)NB_PAD_POS;
+      xl[c] = vh[c] = vl[c] = a2[c] = j6[c] = 0.0f;
+    }
+  }
+  jm[i] = make_float4(xh[0], xh[1], xh[2], mf);
+  jm[n_pad + i] = make_float4(xl[0], xl[1], xl[2], reach);
+  jm[2 * n_pad + i] = make_float4(vh[0], vh[1], vh[2], j6[0]);
+  jm[3 * n_pad + i] = make_float4(vl[0], vl[1], vl[2], j6[1]);
+  jm[4 * n_pad + i] = make_float4(a2[0], a2[1], a2[2], j6[2]);
+}
+
 }  // namespace nbh

@@ -54,7 +54,8 @@ __global__ void correct_kernel(int64_t n, int64_t n_pad, const int32_t* __restri
                                double* __restrict__ v, double* __restrict__ a, double* __restrict__ jk,
                                double* __restrict__ pot, double* __restrict__ ti, double* __restrict__ dt,
                                const double* __restrict__ xp, const double* __restrict__ vp,
-                               nb_dev_status* __restrict__ st) {
+                               nb_dev_status* __restrict__ st, float4* __restrict__ jm, int64_t N,
+                               const double* __restrict__ m) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = list[k];
@@ -63,6 +64,8 @@ __global__ void correct_kernel(int64_t n, int64_t n_pad, const int32_t* __restri
 #pragma unroll
     for (int c = 0; c < 7; ++c) f[c] = F[c * fstride + k];
     nbh::correct_row(i, n_pad, t, f, eta, dt_min, dt_max, x, v, a, jk, pot, ti, dt, xp, vp, st);
+    // the corrected particle's j-memory record (on-the-fly j prediction)
+    if (jm) nbh::write_jm_record(i, N, n_pad, m, x, v, a, jk, dt, jm);
   }
 }
 
@@ -345,12 +348,12 @@ cudaError_t nb_launch_select(nb_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t) {
+cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t, bool write_jm) {
   if (n <= 0) return cudaSuccess;
   c->launches += 1;
   correct_kernel<<<grid_for(n, 128, c->sm_count * 32), 128, 0, c->stream>>>(
       n, c->n_pad, d_list, c->F, c->n_pad, t, c->eta, c->dt_min, c->dt_max, c->x, c->v, c->a, c->jk,
-      c->pot, c->t, c->dt, c->xp, c->vp, c->status);
+      c->pot, c->t, c->dt, c->xp, c->vp, c->status, write_jm ? c->jm : nullptr, c->n, c->m);
   return cudaGetLastError();
 }
 

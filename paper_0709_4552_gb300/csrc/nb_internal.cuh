@@ -118,6 +118,15 @@ struct nb_ctx {
   // mixed path: hi-only differences on (warp, j-tile) pairs that pass the
   // far test (1, the default), or double-single differences everywhere (0)
   int far_tiles;
+  // on-the-fly j prediction (GRAPE's split of Sec. 4.4 steps 3-4, onboard.cu):
+  // the j-memory records jm[5][n_pad] (allocated on first use), valid while
+  // jm_ver == state_ver (every change of the particle state bumps state_ver);
+  // host-loop blocks of n <= jpred_max_n take the fused path
+  float4* jm;
+  int64_t state_ver, jm_ver;
+  int64_t jpred_max_n;
+  bool plist_valid;          // the last force call predicted its own list (nb_compute_forces_at)
+  double t_plist;
   // tuning
   nb_tuning tune_override;   // all-zero = automatic
   nb_tune_entry tune_table[16];
@@ -136,7 +145,8 @@ struct nb_ctx {
 // ---- launchers (integrator.cu) -------------------------------------------
 cudaError_t nb_launch_predict(nb_ctx* c, double t, bool own_time);
 cudaError_t nb_launch_select(nb_ctx* c);    // writes act, sel_cnt[total], sel_min[result]
-cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t);
+// write_jm: also write the corrected rows' j-memory records (c->jm)
+cudaError_t nb_launch_correct(nb_ctx* c, const int32_t* d_list, int64_t n, double t, bool write_jm = false);
 cudaError_t nb_launch_initial_dt(nb_ctx* c);
 cudaError_t nb_launch_energy(nb_ctx* c, const double* d_pot, double* d_out2);
 cudaError_t nb_launch_fill_ident(nb_ctx* c);
@@ -147,12 +157,26 @@ cudaError_t nb_launch_soa_to_aos(const double* src, int64_t stride_src, double* 
 cudaError_t nb_launch_check_list(const int32_t* d_list, int64_t n, int64_t N, unsigned int* d_flag,
                                  cudaStream_t s);
 
+// ---- on-the-fly j prediction (onboard.cu) -----------------------------------
+// j-memory records of the rows in d_list[0..count) (d_list NULL: every row
+// [0, n_pad), padding rows included) from the FP64 state
+cudaError_t nb_launch_jm_write(nb_ctx* c, const int32_t* d_list, int64_t count);
+// one launch: the listed rows predicted to t (FP64 xp, vp and the mixed
+// jA/jB/jC rows) and, with boxes, the far-test boxes of the 128-row tiles
+// from the j-memory, grown by each particle's reach (into c->tbox)
+cudaError_t nb_launch_jm_host_side(nb_ctx* c, const int32_t* d_list, int64_t n, double t, bool boxes);
+// make the j-memory current (allocate, rebuild when the state changed)
+int nb_jm_ensure(nb_ctx* c);
+
 // ---- launchers (force_fp64.cu / force_mixed.cu) ----------------------------
 // forces on the list d_list[0..n) from all N j; results to c->F
 cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
 // ord (optional): processing order of the list positions (spatial order)
 cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
                             const int32_t* ord = nullptr);
+// the mixed item with the j-tiles predicted to T from the j-memory
+cudaError_t nb_forces_mixed_fused(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                                  const int32_t* ord, double T, const float4* boxes);
 // split-j reduction (force_fp64.cu): part[S][7][n] -> F in fixed order, potential sign
 cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit,
                                    int64_t stride);

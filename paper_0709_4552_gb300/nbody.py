@@ -24,12 +24,13 @@ NB_PTR_HOST, NB_PTR_DEVICE = 0, 1
 NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
 NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT = 0, 1, 2
 NB_PERSISTENT_MAX_N = 65536
+NB_JPREDICT_AUTO = -1
 
 # every symbol include/nbody.h declares
 EXPORTS = (
     "nb_create", "nb_destroy", "nb_set_params", "nb_get_params", "nb_default_params", "nb_set_precision",
     "nb_set_j_particles", "nb_set_n", "nb_get_n", "nb_get_particles", "nb_next_block", "nb_predict",
-    "nb_compute_forces", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
+    "nb_compute_forces", "nb_compute_forces_at", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
     "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
@@ -77,6 +78,9 @@ def lib():
         "nb_next_block": (_int, [_vp, _pd, _vp, _pi64]),
         "nb_predict": (_int, [_vp, _d]),
         "nb_compute_forces": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _int]),
+        "nb_compute_forces_at": (_int, [_vp, _d, _vp, _i64, _vp, _vp, _vp, _int]),
+        "nb_set_jpredict": (_int, [_vp, _i64]),
+        "nb_get_jpredict": (_int, [_vp, _pi64]),
         "nb_correct": (_int, [_vp, _vp, _i64, _d, _int]),
         "nb_initial_forces_and_dt": (_int, [_vp]),
         "nb_step": (_int, [_vp, _pd, _pi64]),
@@ -264,6 +268,32 @@ def nb_compute_forces(ctx, i_idx, acc=None, jerk=None, pot=None):
     if ret:
         return keep[1], keep[2], keep[3]
     return acc, jerk, pot
+
+
+def nb_compute_forces_at(ctx, t, i_idx, acc=None, jerk=None, pot=None):
+    """GRAPE-style forces on i_idx at time t: the list predicted alone, the
+    j-particles predicted inside the force kernel (no nb_predict needed).
+    Returns like nb_compute_forces."""
+    n = int(i_idx.shape[0])
+    ret = False
+    if acc is None and jerk is None and pot is None and type(i_idx).__module__ != "torch":
+        acc, jerk, pot = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        ret = True
+    kind, p, keep = _marshal([i_idx, acc, jerk, pot], [np.int32, np.float64, np.float64, np.float64])
+    _check(lib().nb_compute_forces_at(ctx, float(t), p[0], n, p[1], p[2], p[3], kind), "nb_compute_forces_at")
+    if ret:
+        return keep[1], keep[2], keep[3]
+    return acc, jerk, pot
+
+
+def nb_set_jpredict(ctx, max_n):
+    _check(lib().nb_set_jpredict(ctx, int(max_n)), "nb_set_jpredict")
+
+
+def nb_get_jpredict(ctx):
+    v = _i64()
+    _check(lib().nb_get_jpredict(ctx, ctypes.byref(v)), "nb_get_jpredict")
+    return v.value
 
 
 def nb_correct(ctx, i_idx, t):
