@@ -66,6 +66,7 @@ def parse():
                     choices=["c3", "c2", "c4", "c5", "tapp", "c3sweep", "c4init"],
                     help="c3 (default): the timed benchmark; c2/c4/c5: long integrations; tapp: time per "
                          "N-body time unit vs N and the per-task model; one JSON line each")
+    ap.add_argument("--tune-file", default="", help="c4: save the autotuned table to this JSON file")
     ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
     return ap.parse_args()
 
@@ -347,13 +348,25 @@ def run_integration(args):
         res = {}
         finals = {}
         drift64 = None
+        tuned = None
         for mode, prec, name in ((nb.NB_ENSEMBLE_PERSISTENT, nb.NB_MIXED, "persistent_graph"),
+                                 (nb.NB_ENSEMBLE_PERSISTENT, nb.NB_MIXED, "persistent_graph_autotuned"),
                                  (nb.NB_ENSEMBLE_PER_CLUSTER, nb.NB_MIXED, "per_cluster_launches"),
                                  (nb.NB_ENSEMBLE_PERSISTENT, nb.NB_FP64, "persistent_graph_fp64")):
             e = nb.Ensemble(off, eps, prec, 0)
             e.set_params(0.01, 0.01, 2.0 ** -22, t_end)
             e.set_j_particles(0, m, x, v)
             e.initial_forces_and_dt()
+            if name == "persistent_graph":
+                e.tune_clear()   # the default item shape (a table from NB_TUNE_FILE is not used here)
+            if name == "persistent_graph_autotuned":
+                # the item shape timed on 16 block steps of this ensemble's own state (restored),
+                # outside the timed run; the table is saved when --tune-file names a path
+                t0 = time.perf_counter()
+                tuned = e.autotune(16)
+                tuned["tuning_wall_s"] = time.perf_counter() - t0
+                if args.tune_file:
+                    e.tune_save(args.tune_file)
             if name != "per_cluster_launches":
                 ek0_, ep0_ = e.energy()
                 if prec == nb.NB_MIXED:
@@ -392,8 +405,12 @@ def run_integration(args):
             d_gpu = abs(sum(oracle.energy(m[a:b], fx["x"][a:b], fx["v"][a:b], eps[q])) - E0) / abs(E0)
             orc.append({"cluster": int(q), "N": int(b - a), "drift_gpu": d_gpu, "drift_oracle": d_orc})
         dx = np.abs(finals["persistent_graph"]["x"] - finals["per_cluster_launches"]["x"]).max()
+        dx_t = np.abs(finals["persistent_graph"]["x"] - finals["persistent_graph_autotuned"]["x"]).max()
         print(json.dumps({"workload": "c4", "clusters": 512, "N_total": int(off[-1]), "t_end": t_end,
-                          "modes": res,
+                          "modes": res, "autotuned_shape": tuned,
+                          "speedup_autotuned_vs_default_shape": res["persistent_graph"]["wall_s"] /
+                          res["persistent_graph_autotuned"]["wall_s"],
+                          "max_abs_dx_autotuned_vs_default": float(dx_t),
                           "speedup_persistent_vs_per_cluster": res["per_cluster_launches"]["wall_s"] /
                           res["persistent_graph"]["wall_s"],
                           "max_abs_dx_between_modes": float(dx),

@@ -326,12 +326,53 @@ int nb_set_far_tiles(nb_ctx* ctx, int enable);
 int nb_get_far_tiles(nb_ctx* ctx, int* enabled);
 
 /*
- * nb_autotune -- time the supported force launches for the current N and
- * active-block size n on the current state (needs a prediction) and keep the
- * fastest for blocks of about that size.  Writes the chosen configuration
- * (any pointer may be NULL; *n_split = 0 means the automatic split).
+ * nb_autotune -- time the supported force launches of the host-driven path
+ * (i per thread, threads per CTA, j-tile, split-j factor) for the current N
+ * and active-block size n on the current state (needs a prediction) and keep
+ * the fastest in the context's tuning table for systems and blocks within a
+ * factor sqrt(2) of (N, n); every later force call of such a size takes it
+ * (unless nb_set_tuning overrides).  Writes the chosen configuration (any
+ * pointer may be NULL; *n_split = 0 means the automatic split).
  */
 int nb_autotune(nb_ctx* ctx, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split);
+
+/*
+ * nb_ensemble_autotune -- the item shape of the device-driven block steps
+ * (the CUDA-graph loop of one system, or the batched ensemble): i-tile 32, 64
+ * or 128 particles and 2, 4, 8 or 16 force items planned per resident CTA
+ * (which sets the split-j length), each timed on `steps` block steps
+ * (1..4096) of the context's own state, which is restored after every trial
+ * and at the end (the particles, the counters and the schedule are as
+ * before the call).  The fastest goes into the tuning table for batches of
+ * about the same median cluster size (factor sqrt(2)) and cluster count
+ * (factor 2); later nb_ensemble_integrate / nb_integrate(NB_LOOP_GRAPH) calls
+ * use it.  Outputs (any may be NULL): the chosen i-tile and items per CTA,
+ * its time and the time of the default shape (ms for the `steps` steps).
+ * Errors: NB_EINVAL, NB_ESTATE (no particles), NB_ENOMEM, NB_ECUDA,
+ * NB_ENUMERIC (a trial produced NaN/Inf).
+ */
+int nb_ensemble_autotune(nb_ctx* ctx, int64_t steps, int* i_tile, int* item_waves, double* ms_best,
+                         double* ms_default);
+
+/*
+ * nb_tune_save / nb_tune_load -- the context's tuning table as a JSON file:
+ *   {"format": "libnbody tuning table 1", "device": "<name>", "sm_count": S,
+ *    "entries": [{"kind": "single"|"batched", "precision": "fp64"|"mixed",
+ *                 "N_lo", "N_hi", "n_lo", "n_hi", "i_per_thread", "threads",
+ *                 "j_tile", "n_split", "item_waves", "ms"}, ...]}
+ * (for "batched" entries N is the median cluster size, n the cluster count
+ * and "threads" the i-tile).  Loading replaces the table; a file measured on
+ * a GPU with another SM count, or not in this format, is refused with
+ * NB_EINVAL and leaves the table as it was.  nb_create and
+ * nb_ensemble_create load the file named by the environment variable
+ * NB_TUNE_FILE when it is set (silently skipped when it cannot be used).
+ */
+int nb_tune_save(nb_ctx* ctx, const char* path);
+int nb_tune_load(nb_ctx* ctx, const char* path);
+
+/* nb_tune_count / nb_tune_clear -- entries in the tuning table; empty it. */
+int nb_tune_count(nb_ctx* ctx, int* count);
+int nb_tune_clear(nb_ctx* ctx);
 
 /*
  * nb_measure_peaks -- measured arithmetic throughput of the context's GPU:

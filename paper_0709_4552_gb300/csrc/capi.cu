@@ -101,11 +101,8 @@ nb_tuning pick_tuning(const nb_ctx* c, int64_t n) {
                 o.nsplit};
     if (nb_tuning_supported(c->precision, t)) return t;
   }
-  for (int i = 0; i < c->tune_count; ++i) {
-    const nb_tune_entry& e = c->tune_table[i];
-    if (n >= e.n_lo && n < e.n_hi && nb_tuning_supported(c->precision, e.cfg)) return e.cfg;
-  }
-  (void)n;
+  const nb_tune_entry* e = nb_tune_find(c, NB_TUNE_SINGLE, c->n, n);
+  if (e && nb_tuning_supported(c->precision, e->cfg)) return e->cfg;
   return nb_default_tuning(c->precision);
 }
 
@@ -449,6 +446,7 @@ int nb_create(nb_ctx** out, int64_t n_max, int precision, int device, void* cuda
     cudaGetLastError();
     return code;
   }
+  nb_tune_load_env(c);
   *out = c;
   return NB_OK;
 }
@@ -904,13 +902,8 @@ int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_ti
   c->tune_override = saved;
   c->f_valid = false;
   if (best.threads == 0) return fail(c, NB_ECUDA);
-  // table entry for blocks within a factor sqrt(2) of n (replaces an overlapping one)
-  const int64_t lo = (int64_t)(n / 1.41421356), hi = (int64_t)(n * 1.41421356) + 1;
-  int slot = -1;
-  for (int i = 0; i < c->tune_count; ++i)
-    if (c->tune_table[i].n_lo < hi && lo < c->tune_table[i].n_hi) slot = i;
-  if (slot < 0) slot = c->tune_count < 16 ? c->tune_count++ : 15;
-  c->tune_table[slot] = nb_tune_entry{lo, hi, best};
+  // table entry for systems and blocks within a factor sqrt(2) of (N, n)
+  nb_tune_store(c, NB_TUNE_SINGLE, c->n, n, best, best_ms);
   if (i_per_thread) *i_per_thread = best.ipt;
   if (threads) *threads = best.threads;
   if (j_tile) *j_tile = best.jtile;

@@ -86,10 +86,12 @@ struct Batch {
   int cl_bits = 0;                 // bits of a cluster number in the sort keys
   // host
   std::vector<int64_t> h_off;
-  int nt = 128;                    // i-tile (threads per CTA) of the force items: 32 or 128
+  int nt = 128;                    // i-tile (threads per CTA) of the force items: 32, 64 or 128
+  int waves = kItemWaves;          // force items planned per resident CTA (sets the split-j length)
+  int64_t nc_median = 0;           // median cluster size (the autotuner's bin)
   int grid_mixed = 0, grid_fp64 = 0;
   cudaGraphExec_t exec = nullptr;
-  int exec_precision = -1;
+  int64_t exec_key = -1;           // precision, far-tile pass and item shape the graph was built for
   nb_ctx* child = nullptr;         // per-cluster reference path
 };
 
@@ -413,7 +415,7 @@ __device__ __forceinline__ int64_t next_item(unsigned long long* wq, int64_t* s_
 // mixed kernel fits 94 registers (5 CTAs of 128); the item loop must not
 // cost a CTA per SM (117 registers unbounded = 4 CTAs of 128).  The FP64
 // item keeps the default (bounding it to 96 registers spills).
-constexpr int mixed_min_ctas(int nt) { return nt >= 128 ? 5 : 20; }
+constexpr int mixed_min_ctas(int nt) { return nt >= 128 ? 5 : 640 / nt; }
 
 template <int NT, int IPT, int JT>
 __global__ void __launch_bounds__(NT, mixed_min_ctas(NT)) b_force_mixed(
@@ -715,6 +717,44 @@ __global__ void fill_cid(int64_t N, const int64_t* __restrict__ off, int32_t C, 
 }
 
 // build the batch description for clusters h_off[0..C] with softenings eps
+// i-tile and planned items per CTA of the force items; the persistent grids
+// hold as many CTAs as fit on the SMs at that i-tile
+cudaError_t set_shape(nb_ctx* c, Batch* b, int nt, int waves) {
+  int pm = 0, pf = 0;
+  cudaError_t e;
+  if (nt == 32) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, b_force_mixed<32, kMixIPT, kMixJT>, 32, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, b_force_fp64<32, kF64JT>, 32, 0);
+  } else if (nt == 64) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, b_force_mixed<64, kMixIPT, kMixJT>, 64, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, b_force_fp64<64, kF64JT>, 64, 0);
+  } else if (nt == 128) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, b_force_mixed<128, kMixIPT, kMixJT>, 128, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, b_force_fp64<128, kF64JT>, 128, 0);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  b->nt = nt;
+  b->waves = waves;
+  b->grid_mixed = std::max(1, pm) * c->sm_count;
+  b->grid_fp64 = std::max(1, pf) * c->sm_count;
+  return cudaSuccess;
+}
+
+// the item shape for this batch: the autotuner's entry for its median cluster
+// size and cluster count (and the context's precision), else the defaults
+// (32-particle i-tiles for ensembles, 128 for one system; kItemWaves)
+cudaError_t pick_shape(nb_ctx* c, Batch* b) {
+  int nt = b->C > 1 ? 32 : 128, waves = kItemWaves;
+  if (const nb_tune_entry* t = nb_tune_find(c, NB_TUNE_BATCHED, b->nc_median, b->C)) {
+    nt = t->cfg.threads;
+    waves = t->cfg.waves;
+  }
+  if (nt == b->nt && waves == b->waves) return cudaSuccess;
+  return set_shape(c, b, nt, waves);
+}
+
 cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double* eps, Batch** out) {
   Batch* b = new (std::nothrow) Batch();
   if (!b) return cudaErrorMemoryAllocation;
@@ -779,16 +819,13 @@ cudaError_t batch_build(nb_ctx* c, int32_t C, const int64_t* h_off, const double
     fill_cid<<<grid_for(b->N, 256, 4096), 256, 0, c->stream>>>(b->N, b->off, C, b->cid);
     e = cudaGetLastError();
   }
-  b->nt = C > 1 ? 32 : 128;
-  int per_sm = 0;
-  if (e == cudaSuccess)
-    e = b->nt == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<32, kMixIPT, kMixJT>, 32, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_mixed<128, kMixIPT, kMixJT>, 128, 0);
-  b->grid_mixed = std::max(1, per_sm) * c->sm_count;
-  if (e == cudaSuccess)
-    e = b->nt == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<32, kF64JT>, 32, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_force_fp64<128, kF64JT>, 128, 0);
-  b->grid_fp64 = std::max(1, per_sm) * c->sm_count;
+  {
+    std::vector<int64_t> sz(C);
+    for (int32_t q = 0; q < C; ++q) sz[q] = h_off[q + 1] - h_off[q];
+    std::nth_element(sz.begin(), sz.begin() + C / 2, sz.end());
+    b->nc_median = sz[C / 2];
+  }
+  if (e == cudaSuccess) e = set_shape(c, b, C > 1 ? 32 : 128, kItemWaves);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host vectors go out of scope
   if (e != cudaSuccess) {
     batch_free(b);
@@ -820,7 +857,7 @@ cudaError_t plan_only(nb_ctx* c, Batch* b) {
   const int per_cta = b->nt * (mixed ? kMixIPT : 1);
   const int jt = mixed ? kMixJT : kF64JT;
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
-  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, b->waves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
                                     b->ritem_off, b->citem_off, b->wq, b->ctrl,
                                     b->prm, c->status, 0, 0);
@@ -867,6 +904,8 @@ cudaError_t body_after_plan(nb_ctx* c, Batch* b, bool own_time) {
   }
   if (b->nt == 32)
     launch_force<32>(c, b, mixed);
+  else if (b->nt == 64)
+    launch_force<64>(c, b, mixed);
   else
     launch_force<128>(c, b, mixed);
   b_reduce<<<c->sm_count * 8, dim3(32, kRedLanes), 0, c->stream>>>(
@@ -886,7 +925,7 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
                                                  c->dt, b->tnext, b->ch_cnt);
   b_sel_write<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_cnt, b->off,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
-  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, kItemWaves * (int64_t)grid, c->part_elems,
+  b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, b->waves * (int64_t)grid, c->part_elems,
                                     b->itiles, b->nsplit, b->jps, b->item_off, b->part_off, b->pstride,
                                     b->ritem_off, b->citem_off, b->wq, b->ctrl,
                                     b->prm, c->status, handle, use_handle);
@@ -900,8 +939,12 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
   return cudaGetLastError();
 }
 
-cudaError_t build_graph(nb_ctx* c, Batch* b) {
-  if (b->exec && b->exec_precision == c->precision) return cudaSuccess;
+// pick: take the item shape from the autotuner's table (else keep b's shape)
+cudaError_t build_graph(nb_ctx* c, Batch* b, bool pick = true) {
+  cudaError_t e0 = pick ? pick_shape(c, b) : cudaSuccess;
+  if (e0 != cudaSuccess) return e0;
+  const int64_t key = ((int64_t)c->precision << 32) | ((int64_t)c->far_tiles << 31) | ((int64_t)b->nt << 8) | b->waves;
+  if (b->exec && b->exec_key == key) return cudaSuccess;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -943,7 +986,7 @@ cudaError_t build_graph(nb_ctx* c, Batch* b) {
   if (cap) cudaStreamDestroy(cap);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
   cudaGraphDestroy(g);
-  if (e == cudaSuccess) b->exec_precision = c->precision;
+  if (e == cudaSuccess) b->exec_key = key;
   return e;
 }
 
@@ -1152,6 +1195,121 @@ int nb_ensemble_energy(nb_ctx* c, double* ekin, double* epot) {
   return finish_status(c);
 }
 
+// nb_ensemble_autotune: the item shape (i-tile 32/64/128, items per resident
+// CTA 2/4/8/16) timed on `steps` block steps of the context's own state, the
+// state restored after every trial; the fastest goes into the table under the
+// batch's (median cluster size, cluster count) bin
+int nb_ensemble_autotune(nb_ctx* c, int64_t steps, int* i_tile, int* item_waves, double* ms_best,
+                         double* ms_default) {
+  if (!c) return NB_EINVAL;
+  if (steps < 1 || steps > 4096) return NB_EINVAL;
+  if (c->n <= 0) return NB_ESTATE;
+  Batch* b = batch_of(c);
+  if (c->n_clusters == 0 && (!b || b->N != c->n)) {  // a single system's graph loop
+    batch_free(b);
+    c->ens = nullptr;
+    const int64_t off[2] = {0, c->n};
+    const double eps = c->eps;
+    if (batch_build(c, 1, off, &eps, &b) != cudaSuccess) return NB_ECUDA;
+    c->ens = b;
+  }
+  if (c->n_clusters == 0) {
+    const int rs = nb_ensure_sorted(c);
+    if (rs != NB_OK) return rs;
+    const double e2 = c->eps * c->eps;
+    const float e2f = (float)e2;
+    if (cudaMemcpyAsync(b->eps2d, &e2, sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->eps2f, &e2f, sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return NB_ECUDA;
+  }
+  if (c->n < b->N) return NB_ESTATE;
+  const int64_t N = b->N, np = c->n_pad;
+  // the state the trials start from (16 FP64 rows), and a run end past every step
+  double* saved = nullptr;
+  if (cudaMalloc((void**)&saved, (size_t)16 * np * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return NB_ENOMEM;
+  }
+  struct Row {
+    double* p;
+    int k;
+  } rows[] = {{c->m, 1}, {c->x, 3}, {c->v, 3}, {c->a, 3}, {c->jk, 3}, {c->pot, 1}, {c->t, 1}, {c->dt, 1}};
+  auto copy_rows = [&](bool save) -> cudaError_t {
+    int64_t r = 0;
+    for (const Row& q : rows)
+      for (int k = 0; k < q.k; ++k, ++r) {
+        double* live = q.p + k * np;
+        double* keep = saved + r * np;
+        cudaError_t e = cudaMemcpyAsync(save ? keep : live, save ? live : keep, N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+      }
+    return cudaSuccess;
+  };
+  std::vector<double> ht(N);
+  int r = NB_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int nt0 = b->nt, w0 = b->waves;
+  const int64_t steps0 = c->steps;
+  const double inter0 = c->interactions;
+  int best_nt = 0, best_w = 0;
+  float best = 3.4e38f, dflt = -1.0f;
+  if (copy_rows(true) != cudaSuccess ||
+      cudaMemcpyAsync(ht.data(), c->t, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    r = NB_ECUDA;
+  } else {
+    double tmax = 0.0;
+    for (double v : ht) tmax = std::max(tmax, v);
+    const double t_end = (floor(tmax / c->dt_max) + 1.0) * c->dt_max;
+    static const int nts[] = {32, 64, 128};
+    static const int ws[] = {2, 4, 8, 16};
+    for (int a = 0; a < 3 && r == NB_OK; ++a)
+      for (int q = 0; q < 4 && r == NB_OK; ++q) {
+        if (set_shape(c, b, nts[a], ws[q]) != cudaSuccess) { r = NB_ECUDA; break; }
+        // the shape is forced for the trial: the graph is built for it directly
+        if (build_graph(c, b, false) != cudaSuccess) { r = NB_ECUDA; break; }
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && r == NB_OK; ++rep) {  // the first launch uploads the graph
+          if (copy_rows(false) != cudaSuccess || set_params(c, b, t_end, steps) != cudaSuccess ||
+              cudaMemsetAsync(b->ctrl, 0, 4 * sizeof(int64_t), c->stream) != cudaSuccess ||
+              cudaEventRecord(e0, c->stream) != cudaSuccess || cudaGraphLaunch(b->exec, c->stream) != cudaSuccess ||
+              cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            r = NB_ECUDA;
+        }
+        if (r != NB_OK) break;
+        if (finish_status(c) != NB_OK) { r = NB_ENUMERIC; break; }
+        if (nts[a] == (b->C > 1 ? 32 : 128) && ws[q] == kItemWaves) dflt = ms;
+        if (ms < best) {
+          best = ms;
+          best_nt = nts[a];
+          best_w = ws[q];
+        }
+      }
+  }
+  // the caller's state, counters and shape back; the winner into the table
+  if (copy_rows(false) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) r = NB_ECUDA;
+  cudaFree(saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  c->steps = steps0;
+  c->interactions = inter0;
+  c->pred_valid = c->f_valid = false;
+  c->state_ver++;
+  if (set_shape(c, b, nt0, w0) != cudaSuccess && r == NB_OK) r = NB_ECUDA;
+  if (r != NB_OK) return r;
+  nb_tuning cfg{1, best_nt, c->precision == NB_MIXED ? kMixJT : kF64JT, 0, best_w};
+  nb_tune_store(c, NB_TUNE_BATCHED, b->nc_median, b->C, cfg, best);
+  if (i_tile) *i_tile = best_nt;
+  if (item_waves) *item_waves = best_w;
+  if (ms_best) *ms_best = best;
+  if (ms_default) *ms_default = dflt;
+  return NB_OK;
+}
+
 int nb_ensemble_integrate(nb_ctx* c, double t_end, int mode) {
   if (!c || !c->ens || c->n_clusters == 0) return NB_EINVAL;
   Batch* b = batch_of(c);
@@ -1174,6 +1332,7 @@ int nb_ensemble_integrate(nb_ctx* c, double t_end, int mode) {
     ch->n = n;
     ch->pred_valid = ch->f_valid = false;
     ch->perm_valid = false;
+    ch->state_ver++;  // written behind the API: the child's j-memory is stale
     int r = nb_set_params(ch, c->h_ceps[q], c->eta, c->dt_min, c->dt_max);
     if (r == NB_OK) r = nb_integrate(ch, t_end, 0);
     if (r != NB_OK) return r;

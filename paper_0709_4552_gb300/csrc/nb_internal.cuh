@@ -51,14 +51,23 @@ struct nb_dev_status {
 
 struct nb_tuning {
   int ipt;      // i-particles per thread
-  int threads;  // threads per CTA
+  int threads;  // threads per CTA (batched items: the i-tile)
   int jtile;    // j-particles per shared-memory tile
   int nsplit;   // split-j factor (0 = automatic)
+  int waves;    // batched items: force items planned per resident CTA (0 = default)
 };
 
+// the autotuner's table (tune.cu): the fastest measured launch per workload bin
+#define NB_TUNE_SINGLE 0   // force launch of the host-driven path, bins of (N, n)
+#define NB_TUNE_BATCHED 1  // items of the device-driven loops, bins of (median N_c, clusters C)
+#define NB_TUNE_MAX 64
 struct nb_tune_entry {
-  int64_t n_lo, n_hi;  // active-block size range this entry covers
+  int kind;             // NB_TUNE_SINGLE / NB_TUNE_BATCHED
+  int precision;
+  int64_t N_lo, N_hi;   // N (single) or median cluster size (batched), [lo, hi)
+  int64_t n_lo, n_hi;   // active block n (single) or cluster count C (batched), [lo, hi)
   nb_tuning cfg;
+  double ms;            // measured time of cfg when it was chosen
 };
 
 struct nb_ctx {
@@ -129,7 +138,7 @@ struct nb_ctx {
   double t_plist;
   // tuning
   nb_tuning tune_override;   // all-zero = automatic
-  nb_tune_entry tune_table[16];
+  nb_tune_entry tune_table[NB_TUNE_MAX];
   int tune_count;
 
   // ensemble
@@ -202,6 +211,14 @@ cudaError_t nb_gather_rows(nb_ctx* c, const double* src, int rows, int64_t first
 cudaError_t nb_launch_tile_boxes(nb_ctx* c);  // tbox from the predicted (permuted) j-store
 // processing order of a list of slots: positions sorted by slot (device array of n positions)
 cudaError_t nb_list_order(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** ord);
+
+// tune.cu: the autotuner's table
+// the entry of kind for (N, n) and the context's precision, or null
+const nb_tune_entry* nb_tune_find(const nb_ctx* c, int kind, int64_t N, int64_t n);
+// record cfg for the bin around (N, n) (replaces an overlapping entry)
+void nb_tune_store(nb_ctx* c, int kind, int64_t N, int64_t n, const nb_tuning& cfg, double ms);
+// the table of the file named by NB_TUNE_FILE, if that is set (errors ignored)
+void nb_tune_load_env(nb_ctx* c);
 
 // capi.cu: (re)compute the resident spatial order when it is due (mixed path)
 int nb_ensure_sorted(nb_ctx* c);

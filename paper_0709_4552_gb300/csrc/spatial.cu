@@ -284,6 +284,7 @@ __global__ void gather_rows(const double* __restrict__ src, int rows, int64_t n_
 
 // reorder every state row by src (new row s = old row src[s]) in place
 cudaError_t reorder_state(nb_ctx* c, const int32_t* src) {
+  c->state_ver++;  // rows move: any row-keyed copy of the state (the j-memory) is stale
   if (!c->pscratch) {
     cudaError_t e = cudaMalloc(&c->pscratch, (size_t)kStateRows * c->n_pad * sizeof(double));
     if (e != cudaSuccess) {

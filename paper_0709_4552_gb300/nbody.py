@@ -33,7 +33,8 @@ EXPORTS = (
     "nb_compute_forces", "nb_compute_forces_at", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
-    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
+    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
+    "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
 
@@ -96,6 +97,11 @@ def lib():
         "nb_set_far_tiles": (_int, [_vp, _int]),
         "nb_get_far_tiles": (_int, [_vp, _pint]),
         "nb_autotune": (_int, [_vp, _i64, _pint, _pint, _pint, _pint]),
+        "nb_ensemble_autotune": (_int, [_vp, _i64, _pint, _pint, _pd, _pd]),
+        "nb_tune_save": (_int, [_vp, ctypes.c_char_p]),
+        "nb_tune_load": (_int, [_vp, ctypes.c_char_p]),
+        "nb_tune_count": (_int, [_vp, _pint]),
+        "nb_tune_clear": (_int, [_vp]),
         "nb_ensemble_create": (_int, [ctypes.POINTER(_vp), _i32, _vp, _vp, _int, _int, _vp]),
         "nb_measure_peaks": (_int, [_vp, _pd, _pd, _pd]),
         "nb_ensemble_initial_forces_and_dt": (_int, [_vp]),
@@ -378,6 +384,34 @@ def nb_autotune(ctx, n):
     v = [_int() for _ in range(4)]
     _check(lib().nb_autotune(ctx, int(n), *[ctypes.byref(x) for x in v]), "nb_autotune")
     return dict(i_per_thread=v[0].value, threads=v[1].value, j_tile=v[2].value, n_split=v[3].value)
+
+
+def nb_ensemble_autotune(ctx, steps=16):
+    """Times the device-driven item shapes on `steps` block steps of the
+    context's state (restored) and keeps the fastest in its tuning table."""
+    it, w = _int(), _int()
+    mb, md = _d(), _d()
+    _check(lib().nb_ensemble_autotune(ctx, int(steps), ctypes.byref(it), ctypes.byref(w), ctypes.byref(mb),
+                                      ctypes.byref(md)), "nb_ensemble_autotune")
+    return dict(i_tile=it.value, item_waves=w.value, ms_best=mb.value, ms_default=md.value)
+
+
+def nb_tune_save(ctx, path):
+    _check(lib().nb_tune_save(ctx, os.fsencode(path)), "nb_tune_save")
+
+
+def nb_tune_load(ctx, path):
+    _check(lib().nb_tune_load(ctx, os.fsencode(path)), "nb_tune_load")
+
+
+def nb_tune_count(ctx):
+    v = _int()
+    _check(lib().nb_tune_count(ctx, ctypes.byref(v)), "nb_tune_count")
+    return v.value
+
+
+def nb_tune_clear(ctx):
+    _check(lib().nb_tune_clear(ctx), "nb_tune_clear")
 
 
 def nb_measure_peaks(ctx):

@@ -1,0 +1,138 @@
+"""The autotuner as part of the path: nb_autotune (the host-driven force
+launch, binned by N and n) and nb_ensemble_autotune (the item shape of the
+device-driven loops and ensembles, binned by median cluster size and cluster
+count), the table in a JSON file (nb_tune_save / nb_tune_load / NB_TUNE_FILE),
+and the integrations under a tuned table against the oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0709_4552_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _ensemble_ics(sizes, seed):
+    ms, xs, vs, eps = [], [], [], []
+    for q, n in enumerate(sizes):
+        m, x, v = inputs.plummer(int(n), seed + q, "salpeter")
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+        eps.append(1.0 / (4.0 * n ** (1.0 / 3.0)))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return off, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), np.array(eps)
+
+
+def _ens(nb, prec, off, m, x, v, eps, t_end):
+    e = nb.Ensemble(off, eps, prec, 0)
+    e.set_params(0.01, 0.01, 2.0 ** -22, t_end)
+    e.set_j_particles(0, m, x, v)
+    e.initial_forces_and_dt()
+    return e
+
+
+def test_table_file_round_trip(nbl, tmp_path):
+    N = 20000
+    m, x, v = inputs.plummer(N, 51)
+    path1, path2 = str(tmp_path / "t1.json"), str(tmp_path / "t2.json")
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_j_particles(0, m, x, v)
+        s.predict(0.0)
+        cfg = s.autotune(700)
+        assert s.tune_count() == 1
+        nbl.nb_tune_save(s.ctx, path1)
+    doc = json.load(open(path1))
+    assert doc["format"] == "libnbody tuning table 1" and len(doc["entries"]) == 1
+    ent = doc["entries"][0]
+    assert ent["kind"] == "single" and ent["precision"] == "mixed"
+    assert ent["N_lo"] <= N < ent["N_hi"] and ent["n_lo"] <= 700 < ent["n_hi"]
+    assert (ent["i_per_thread"], ent["threads"], ent["j_tile"], ent["n_split"]) == \
+        (cfg["i_per_thread"], cfg["threads"], cfg["j_tile"], cfg["n_split"])
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        assert s.tune_count() == 0
+        nbl.nb_tune_load(s.ctx, path1)
+        assert s.tune_count() == 1
+        nbl.nb_tune_save(s.ctx, path2)
+    assert json.load(open(path2)) == doc
+    # the environment variable is read when a context is made
+    os.environ["NB_TUNE_FILE"] = path1
+    try:
+        with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+            assert s.tune_count() == 1
+    finally:
+        del os.environ["NB_TUNE_FILE"]
+
+
+def test_table_refuses_foreign_or_broken_files(nbl, tmp_path):
+    with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
+        good = {"format": "libnbody tuning table 1", "device": "x", "sm_count": 0, "entries": []}
+        bad_sm = str(tmp_path / "sm.json")
+        json.dump(dict(good, sm_count=1), open(bad_sm, "w"))
+        broken = str(tmp_path / "broken.json")
+        open(broken, "w").write('{"format": "libnbody tuning table 1", "entries": [')
+        for p in (bad_sm, broken, str(tmp_path / "missing.json")):
+            with pytest.raises(nbl.NBodyError) as err:
+                nbl.nb_tune_load(s.ctx, p)
+            assert err.value.code == nbl.NB_EINVAL
+        assert s.tune_count() == 0
+
+
+def test_ensemble_autotune_restores_the_state(nbl):
+    sizes = [300, 90, 700, 128, 1000]
+    off, m, x, v, eps = _ensemble_ics(sizes, 710)
+    N = int(off[-1])
+    with _ens(nbl, nbl.NB_MIXED, off, m, x, v, eps, 2.0 ** -5) as e:
+        before = e.get_particles(0, N)
+        c0 = e.get_counters()
+        res = e.autotune(8)
+        assert res["i_tile"] in (32, 64, 128) and res["item_waves"] in (2, 4, 8, 16)
+        assert 0 < res["ms_best"] <= res["ms_default"]
+        assert e.tune_count() == 1
+        after = e.get_particles(0, N)
+        assert e.get_counters()["block_steps"] == c0["block_steps"]
+    for k in ("x", "v", "a", "jerk", "t", "dt"):
+        assert np.array_equal(before[k], after[k]), k
+
+
+def test_ensemble_matches_oracle_under_tuned_table(nbl):
+    # the FP64 ensemble of the oracle test, integrated with the tuned item shape
+    sizes = [300, 90, 700, 128]
+    off, m, x, v, eps = _ensemble_ics(sizes, 700)
+    t_end = 2.0 ** -5
+    N = int(off[-1])
+    with _ens(nbl, nbl.NB_FP64, off, m, x, v, eps, t_end) as e:
+        res = e.autotune(8)
+        e.integrate(t_end)
+        st = e.get_particles(0, N)
+    print("tuned shape", res)
+    for q in range(len(sizes)):
+        a, b = off[q], off[q + 1]
+        r = oracle.hermite_run(m[a:b], x[a:b], v[a:b], eps[q], 0.01, 2.0 ** -22, t_end, t_end, compensated=True)
+        assert np.array_equal(st["dt"][a:b], r["dt"])
+        assert np.abs(st["x"][a:b] - r["x"]).max() < 1e-11
+
+
+def test_graph_loop_under_tuned_table(nbl):
+    # one system's graph loop tuned the same way; mixed drift within 2x the oracle's
+    N, eps, t_end = 2048, 1 / 256, 2.0 ** -4
+    m, x, v = inputs.plummer(N, 811, "salpeter")
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, t_end)
+        s.set_j_particles(0, m, x, v)
+        s.initial_forces_and_dt()
+        res = nbl.nb_ensemble_autotune(s.ctx, 8)
+        assert res["i_tile"] in (32, 64, 128)
+        k0, w0 = s.energy()
+        s.integrate(t_end, use_graph=True)
+        k1, w1 = s.energy()
+        st = s.get_particles(0, N)
+    assert np.all(st["t"] == t_end)
+    E0 = sum(oracle.energy(m, x, v, eps))
+    r = oracle.hermite_run(m, x, v, eps, 0.01, 2.0 ** -22, t_end, t_end)
+    d_orc = abs(sum(oracle.energy(m, r["x"], r["v"], eps)) - E0) / abs(E0)
+    d_gpu = abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)
+    assert d_gpu <= 2 * d_orc + 1e-9, (d_gpu, d_orc)
