@@ -202,6 +202,76 @@ int nb_set_jpredict(nb_ctx* ctx, int64_t max_n);
 /* nb_get_jpredict -- the largest block that takes the on-the-fly prediction. */
 int nb_get_jpredict(nb_ctx* ctx, int64_t* max_n);
 
+/* ---- exchange between ranks: the copy (Sec. 4.2) and ring (Sec. 4.3)
+ * algorithms, one context per rank, driven by the package's distributed
+ * module.  These calls share the list staging of nb_compute_forces and
+ * nb_correct: make them between block steps, not between a force call and
+ * its nb_correct (except nb_set_forces, which feeds nb_correct). ---------- */
+
+/*
+ * nb_get_particles_idx -- particles idx[0..n) (ascending, unique, < N) out
+ * of the state, in list order: m[n], x, v, a, jerk [n][3], pot, t, dt [n]
+ * (any output NULL = skipped).  The copy algorithm gathers its corrected
+ * block with it before the all-gather.  Errors: NB_EINVAL, NB_ECUDA.
+ */
+int nb_get_particles_idx(nb_ctx* ctx, const int32_t* idx, int64_t n, double* m, double* x, double* v, double* a,
+                         double* jerk, double* pot, double* t, double* dt, int ptr_kind);
+
+/*
+ * nb_set_particles_idx -- write particles idx[0..n) (ascending, unique,
+ * < N) of the state from the list-ordered arrays (NULL = unchanged): the copy
+ * algorithm's update of every rank's full copy with the blocks the other
+ * ranks corrected.  Invalidates the prediction.  Errors: NB_EINVAL
+ * (non-finite host value, bad list), NB_ECUDA.
+ */
+int nb_set_particles_idx(nb_ctx* ctx, const int32_t* idx, int64_t n, const double* m, const double* x,
+                         const double* v, const double* a, const double* jerk, const double* pot, const double* t,
+                         const double* dt, int ptr_kind);
+
+/*
+ * nb_get_predicted -- predicted positions and velocities xp, vp [n][3] of
+ * particles idx[0..n) at the time of the last nb_predict: the ring
+ * algorithm's active block leaves its rank with them.  Errors: NB_EINVAL,
+ * NB_ESTATE (no current prediction), NB_ECUDA.
+ */
+int nb_get_predicted(nb_ctx* ctx, const int32_t* idx, int64_t n, double* xp, double* vp, int ptr_kind);
+
+/*
+ * nb_forces_on -- Eq. 3 on n particles held elsewhere (the ring algorithm's
+ * visiting block, Sec. 4.3): positions xi and velocities vi [n][3] at the
+ * block time, summed over this context's j-particles at their last
+ * nb_predict (the same arithmetic as nb_compute_forces, in the context's
+ * precision).  gid[k] (nullable) is particle k's global index; a j-particle
+ * whose global index gid_base + (its index here) equals it is the self pair
+ * and is excluded.  Outputs acc, jerk [n][3], pot [n] (any may be NULL),
+ * overwritten, or with accumulate != 0 added onto what they hold (the
+ * block's running sums).  n <= the context's padded capacity (n_max rounded
+ * up to 1024).  Errors: NB_EINVAL, NB_ESTATE (no prediction), NB_ENOMEM,
+ * NB_ECUDA.
+ */
+int nb_forces_on(nb_ctx* ctx, int64_t n, const double* xi, const double* vi, const int64_t* gid, int64_t gid_base,
+                 double* acc, double* jerk, double* pot, int accumulate, int ptr_kind);
+
+/*
+ * nb_set_forces -- install forces computed elsewhere (the ring algorithm's
+ * sums, back home after the last shift) as the results for the particles
+ * idx[0..n) (ascending, unique), for the nb_correct(idx, t) that follows;
+ * needs the prediction to t of these particles (nb_predict).  Errors:
+ * NB_EINVAL (NULL or non-finite value), NB_ESTATE, NB_ECUDA.
+ */
+int nb_set_forces(nb_ctx* ctx, const int32_t* idx, int64_t n, const double* acc, const double* jerk,
+                  const double* pot, int ptr_kind);
+
+/*
+ * nb_set_initial_forces -- Sec. 4.1 step 1 with forces summed elsewhere (the
+ * ring algorithm's first circuit, when no rank holds all N): every
+ * particle's acceleration, jerk and potential from acc, jerk [N][3], pot [N]
+ * (particle order), t_i = 0, and the initial steps of
+ * nb_initial_forces_and_dt.  Errors: NB_EINVAL, NB_ESTATE (N == 0),
+ * NB_ENUMERIC, NB_ECUDA.
+ */
+int nb_set_initial_forces(nb_ctx* ctx, const double* acc, const double* jerk, const double* pot, int ptr_kind);
+
 /*
  * nb_correct -- Sec. 4.1 step 5: 4th-order Hermite correction of the n
  * particles i_idx (the list of the preceding nb_compute_forces or

@@ -68,7 +68,8 @@ void free_ctx(nb_ctx* c) {
   void* dptrs[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt, c->xp, c->vp, c->jA, c->jB,
                    c->jC, c->F, c->part, c->act, c->ident, c->ulist, c->sel_min, c->sel_cnt, c->red,
                    c->status, c->d_offsets, c->d_ceps, c->perm, c->iperm, c->skey[0], c->skey[1],
-                   c->sval[0], c->sval[1], c->shist, c->tbox, c->mlist, c->pscratch, c->jm};
+                   c->sval[0], c->sval[1], c->shist, c->tbox, c->mlist, c->pscratch, c->jm,
+                   c->ext_x, c->ext_v, c->ext_A, c->ext_B, c->ext_C, c->ext_self, c->ext_ident, c->ext_gid};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -667,6 +668,196 @@ int nb_get_jpredict(nb_ctx* c, int64_t* max_n) {
   if (!c || !max_n) return NB_EINVAL;
   *max_n = c->jpred_max_n;
   return NB_OK;
+}
+
+// ---- particle and force exchange of the parallel algorithms (Sec. 4.2-4.3) ----
+
+int nb_get_particles_idx(nb_ctx* c, const int32_t* idx, int64_t n, double* m, double* x, double* v, double* a,
+                         double* jerk, double* pot, double* t, double* dt, int ptr_kind) {
+  NB_ENTER(c);
+  if (n < 0 || n > c->n || (n > 0 && !idx) || (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  const int32_t* slots = nullptr;
+  int r = caller_list(c, idx, n, ptr_kind, &slots);
+  if (r) return r;
+  const double* src[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt};
+  double* dst[] = {m, x, v, a, jerk, pot, t, dt};
+  const int rows[] = {1, 3, 3, 3, 3, 1, 1, 1};
+  for (int q = 0; q < 8; ++q) {
+    if (!dst[q]) continue;
+    if (ptr_kind == NB_PTR_DEVICE) {
+      NB_CUDA(c, nb_launch_gather_slots(c, slots, n, src[q], rows[q], dst[q]));
+    } else {
+      NB_CUDA(c, nb_launch_gather_slots(c, slots, n, src[q], rows[q], c->part));
+      NB_CUDA(c, cudaMemcpyAsync(dst[q], c->part, rows[q] * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
+int nb_set_particles_idx(nb_ctx* c, const int32_t* idx, int64_t n, const double* m, const double* x,
+                         const double* v, const double* a, const double* jerk, const double* pot, const double* t,
+                         const double* dt, int ptr_kind) {
+  NB_ENTER(c);
+  if (n < 0 || n > c->n || (n > 0 && !idx) || (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  const double* src[] = {m, x, v, a, jerk, pot, t, dt};
+  double* dst[] = {c->m, c->x, c->v, c->a, c->jk, c->pot, c->t, c->dt};
+  const int rows[] = {1, 3, 3, 3, 3, 1, 1, 1};
+  if (ptr_kind == NB_PTR_HOST)
+    for (int q = 0; q < 8; ++q)
+      if (src[q])
+        for (int64_t i = 0; i < rows[q] * n; ++i)
+          if (!isfinite(src[q][i])) return fail(c, NB_EINVAL);
+  const int32_t* slots = nullptr;
+  int r = caller_list(c, idx, n, ptr_kind, &slots);
+  if (r) return r;
+  for (int q = 0; q < 8; ++q) {
+    if (!src[q]) continue;
+    const double* s = src[q];
+    if (ptr_kind == NB_PTR_HOST) {
+      NB_CUDA(c, cudaMemcpyAsync(c->part, src[q], rows[q] * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      s = c->part;
+    }
+    NB_CUDA(c, nb_launch_scatter_slots(c, slots, n, s, rows[q], dst[q]));
+  }
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->pred_valid = false;
+  c->f_valid = false;
+  c->plist_valid = false;
+  c->state_ver++;
+  return NB_OK;
+}
+
+int nb_get_predicted(nb_ctx* c, const int32_t* idx, int64_t n, double* xp, double* vp, int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n || (n > 0 && !idx) || (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  const int32_t* slots = nullptr;
+  int r = caller_list(c, idx, n, ptr_kind, &slots);
+  if (r) return r;
+  const double* src[] = {c->xp, c->vp};
+  double* dst[] = {xp, vp};
+  for (int q = 0; q < 2; ++q) {
+    if (!dst[q]) continue;
+    if (ptr_kind == NB_PTR_DEVICE) {
+      NB_CUDA(c, nb_launch_gather_slots(c, slots, n, src[q], 3, dst[q]));
+    } else {
+      NB_CUDA(c, nb_launch_gather_slots(c, slots, n, src[q], 3, c->part));
+      NB_CUDA(c, cudaMemcpyAsync(dst[q], c->part, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
+int nb_forces_on(nb_ctx* c, int64_t n, const double* xi, const double* vi, const int64_t* gid, int64_t gid_base,
+                 double* acc, double* jerk, double* pot, int accumulate, int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n_pad || (n > 0 && (!xi || !vi)) || (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  if (ptr_kind == NB_PTR_HOST)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (!isfinite(xi[i]) || !isfinite(vi[i])) return fail(c, NB_EINVAL);
+  NB_CUDA(c, nb_ext_reserve(c, n));
+  const double* dx = xi;
+  const double* dv = vi;
+  const int64_t* dg = gid;
+  if (ptr_kind == NB_PTR_HOST) {  // staged: the kernel below reads them before the force items reuse part
+    NB_CUDA(c, cudaMemcpyAsync(c->part, xi, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(c->part + 3 * n, vi, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (gid) NB_CUDA(c, cudaMemcpyAsync(c->ext_gid, gid, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    dx = c->part;
+    dv = c->part + 3 * n;
+    dg = gid ? c->ext_gid : nullptr;
+  }
+  NB_CUDA(c, nb_launch_ext_prepare(c, n, dx, dv, dg, gid_base));
+  NB_CUDA(c, nb_forces_ext(c, n, pick_tuning(c, n)));
+  c->f_valid = false;  // F holds the block's sums, not a list of this context
+  c->interactions += (double)n * (double)c->n;
+  if (ptr_kind == NB_PTR_DEVICE) {
+    NB_CUDA(c, nb_launch_forces_out(c, n, acc, jerk, pot, accumulate));
+    return NB_OK;
+  }
+  // host outputs through part: acc [0, 3n), jerk [3n, 6n), pot [6n, 7n)
+  double* sa = acc ? c->part : nullptr;
+  double* sj = jerk ? c->part + 3 * n : nullptr;
+  double* sp = pot ? c->part + 6 * n : nullptr;
+  if (accumulate) {
+    if (sa) NB_CUDA(c, cudaMemcpyAsync(sa, acc, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (sj) NB_CUDA(c, cudaMemcpyAsync(sj, jerk, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (sp) NB_CUDA(c, cudaMemcpyAsync(sp, pot, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  NB_CUDA(c, nb_launch_forces_out(c, n, sa, sj, sp, accumulate));
+  if (sa) NB_CUDA(c, cudaMemcpyAsync(acc, sa, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (sj) NB_CUDA(c, cudaMemcpyAsync(jerk, sj, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (sp) NB_CUDA(c, cudaMemcpyAsync(pot, sp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NB_OK;
+}
+
+int nb_set_forces(nb_ctx* c, const int32_t* idx, int64_t n, const double* acc, const double* jerk,
+                  const double* pot, int ptr_kind) {
+  NB_SINGLE(c);
+  if (n < 0 || n > c->n || (n > 0 && (!idx || !acc || !jerk || !pot)) ||
+      (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE))
+    return fail(c, NB_EINVAL);
+  if (n == 0) return NB_OK;
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  if (ptr_kind == NB_PTR_HOST)
+    for (int64_t i = 0; i < n; ++i)
+      if (!isfinite(acc[3 * i]) || !isfinite(acc[3 * i + 1]) || !isfinite(acc[3 * i + 2]) ||
+          !isfinite(jerk[3 * i]) || !isfinite(jerk[3 * i + 1]) || !isfinite(jerk[3 * i + 2]) || !isfinite(pot[i]))
+        return fail(c, NB_EINVAL);
+  const int32_t* d_list = nullptr;
+  int r = caller_list(c, idx, n, ptr_kind, &d_list);
+  if (r) return r;
+  if ((r = put_vec(c, acc, c->F, 0, n, ptr_kind))) return r;
+  if ((r = put_vec(c, jerk, c->F + 3 * c->n_pad, 0, n, ptr_kind))) return r;
+  if ((r = put_scalar(c, pot, c->F + 6 * c->n_pad, 0, n, ptr_kind))) return r;
+  if (ptr_kind == NB_PTR_HOST) NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->f_n = n;
+  c->f_valid = true;
+  c->f_list = d_list;
+  c->plist_valid = false;
+  return NB_OK;
+}
+
+int nb_set_initial_forces(nb_ctx* c, const double* acc, const double* jerk, const double* pot, int ptr_kind) {
+  NB_SINGLE(c);
+  if (!acc || !jerk || !pot || (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE)) return fail(c, NB_EINVAL);
+  const int64_t n = c->n;
+  if (n <= 0) return fail(c, NB_ESTATE);
+  if (ptr_kind == NB_PTR_HOST)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (!isfinite(acc[i]) || !isfinite(jerk[i]) || (i < n && !isfinite(pot[i]))) return fail(c, NB_EINVAL);
+  // particle order in, rows of the resident order out
+  const int32_t* slots = c->perm_valid ? c->iperm : c->ident;
+  const double* src[] = {acc, jerk, pot};
+  double* dst[] = {c->F, c->F + 3 * c->n_pad, c->F + 6 * c->n_pad};
+  const int rows[] = {3, 3, 1};
+  for (int q = 0; q < 3; ++q) {
+    const double* s = src[q];
+    if (ptr_kind == NB_PTR_HOST) {
+      NB_CUDA(c, cudaMemcpyAsync(c->part, src[q], rows[q] * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      s = c->part;
+    }
+    NB_CUDA(c, nb_launch_scatter_slots(c, slots, n, s, rows[q], dst[q]));
+  }
+  NB_CUDA(c, nb_launch_initial_dt(c));
+  c->pred_valid = false;
+  c->f_valid = false;
+  c->plist_valid = false;
+  c->state_ver++;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return device_status_code(c, nullptr) == NB_ENUMERIC ? fail(c, NB_ENUMERIC) : NB_OK;
 }
 
 int nb_correct(nb_ctx* c, const int32_t* i_idx, int64_t n, double t, int ptr_kind) {

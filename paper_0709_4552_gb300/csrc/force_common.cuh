@@ -125,6 +125,23 @@ struct FusedSmem {
   float2 C[JT];
 };
 
+// Where an item's i-particles come from.  By default they are the j-store
+// rows its list names (every particle's own predicted row).  For forces on
+// particles held elsewhere -- the visiting block of the ring algorithm
+// (Sec. 4.3), whose positions and velocities arrive from another rank -- the
+// list indexes separate arrays instead, and self[k] gives the j-store slot of
+// list position k's particle when this store holds it (else -1), which keeps
+// the self pair excluded by index.
+struct ISrc {
+  const float4* __restrict__ A = nullptr;  // mixed: (x_hi, m), (x_lo, vx), (vy, vz) like jA/jB/jC
+  const float4* __restrict__ B = nullptr;
+  const float2* __restrict__ C = nullptr;
+  const double* __restrict__ x = nullptr;  // FP64: SoA rows x[3][stride], v[3][stride]
+  const double* __restrict__ v = nullptr;
+  int64_t stride = 0;
+  const int32_t* __restrict__ self = nullptr;
+};
+
 struct FusedArgs {
   const float4* __restrict__ jm = nullptr;  // R0..R4 rows, stride n_pad
   int64_t stride = 0;
@@ -425,7 +442,7 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
                                            float eps2, double* __restrict__ out, int64_t ostride,
                                            bool finalize, const float4* __restrict__ tbox = nullptr,
                                            const int32_t* __restrict__ ord = nullptr, int64_t box_origin = 0,
-                                           const FusedArgs fa = FusedArgs()) {
+                                           const FusedArgs fa = FusedArgs(), const ISrc is = ISrc()) {
   constexpr bool kFusedLoad = SM::kFused;
   // list: j-store slots of the i-particles.  ord (optional): the list
   // positions in processing order (a caller's list visited in spatial
@@ -469,10 +486,21 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
     if (pos >= n) pos = n - 1;
     if (ord) pos = ord[pos];
     int64_t p = list[pos];
-    p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
-    self[k] = p;  // j-store slot of this i
-    const float4 A = jA[p], B = jB[p];
-    const float2 C = jC[p];
+    float4 A, B;
+    float2 C;
+    if (is.A) {  // a particle held elsewhere: list positions index the i arrays (n long)
+      p = p < 0 ? 0 : (p >= n ? n - 1 : p);
+      A = is.A[p];
+      B = is.B[p];
+      C = is.C[p];
+      self[k] = is.self ? is.self[pos] : -1;
+    } else {
+      p = p < 0 ? 0 : (p >= idx_hi ? idx_hi - 1 : p);  // a bad list never reads out of bounds
+      self[k] = p;  // j-store slot of this i
+      A = jA[p];
+      B = jB[p];
+      C = jC[p];
+    }
     xh[k][0] = A.x; xh[k][1] = A.y; xh[k][2] = A.z;
     xl[k][0] = B.x; xl[k][1] = B.y; xl[k][2] = B.z;
     vi[k][0] = B.w; vi[k][1] = C.x; vi[k][2] = C.y;
@@ -659,17 +687,27 @@ __device__ __forceinline__ void fp64_item(Fp64Smem<JT>& sm, const double* __rest
                                           int64_t n_pad, int64_t jlo, int64_t jhi,
                                           const int32_t* __restrict__ list, int64_t n, int64_t ibase,
                                           double eps2, double* __restrict__ out, int64_t ostride,
-                                          bool finalize) {
+                                          bool finalize, const ISrc is = ISrc()) {
   const int tid = threadIdx.x;
   const int64_t pos0 = ibase + tid;
   const int64_t pos = pos0 < n ? pos0 : n - 1;
   int64_t self = list[pos];
-  self = self < 0 ? 0 : (self >= n_pad ? n_pad - 1 : self);  // a bad list never reads out of bounds
   double xi[3], vi[3];
+  if (is.x) {  // a particle held elsewhere (see ISrc)
+    self = self < 0 ? 0 : (self >= n ? n - 1 : self);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    xi[c] = xp[c * n_pad + self];
-    vi[c] = vp[c * n_pad + self];
+    for (int c = 0; c < 3; ++c) {
+      xi[c] = is.x[c * is.stride + self];
+      vi[c] = is.v[c * is.stride + self];
+    }
+    self = is.self ? is.self[pos] : -1;
+  } else {
+    self = self < 0 ? 0 : (self >= n_pad ? n_pad - 1 : self);  // a bad list never reads out of bounds
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xi[c] = xp[c * n_pad + self];
+      vi[c] = vp[c * n_pad + self];
+    }
   }
   double hi[7], lo[7];
 #pragma unroll

@@ -12,7 +12,7 @@ template <int NT, int JT>
 __global__ void __launch_bounds__(NT) force_fp64_kernel(
     const double* __restrict__ xp, const double* __restrict__ vp, const double* __restrict__ m,
     int64_t n_pad, int64_t N, const int32_t* __restrict__ list, int64_t n, int64_t tiles,
-    double eps2, double* __restrict__ out, int64_t ostride, int finalize) {
+    double eps2, double* __restrict__ out, int64_t ostride, int finalize, const nbk::ISrc is) {
   __shared__ nbk::Fp64Smem<JT> sm;
   const int split = blockIdx.y;
   // j-range of this split, cut at N: the item fills the rest of the last
@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(NT) force_fp64_kernel(
   const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, N);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::fp64_item<NT, JT>(sm, xp, vp, m, n_pad, jlo, jhi, list, n, (int64_t)blockIdx.x * NT, eps2, o, ostride,
-                         finalize != 0);
+                         finalize != 0, is);
 }
 
 // split-j reduction: F[c][k] = sum over s = 0..S-1 (in this order) of
@@ -55,7 +55,7 @@ __global__ void split_reduce_kernel(const double* __restrict__ part, int64_t str
 }
 
 template <int NT, int JT>
-cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg) {
+cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg, const nbk::ISrc& is) {
   static int per_sm = 0;  // resident CTAs per SM of this instantiation
   if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_fp64_kernel<NT, JT>, NT, 0) !=
                          cudaSuccess)
@@ -73,7 +73,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
   dim3 grid((unsigned)itiles, (unsigned)nsplit);
   c->launches += fin ? 1 : 2;
   force_fp64_kernel<NT, JT><<<grid, NT, 0, c->stream>>>(c->xp, c->vp, c->m, c->n_pad, c->n, d_list, n,
-                                                        tiles, c->eps * c->eps, out, ostride, fin ? 1 : 0);
+                                                        tiles, c->eps * c->eps, out, ostride, fin ? 1 : 0, is);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
@@ -146,10 +146,12 @@ int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg, int per_sm) 
 }
 
 #define NB_FP64_CASE(NT_, JT_) \
-  if (cfg.threads == NT_ && cfg.jtile == JT_) return launch<NT_, JT_>(c, d_list, n, cfg);
+  if (cfg.threads == NT_ && cfg.jtile == JT_) return launch<NT_, JT_>(c, d_list, n, cfg, is);
 
-cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg) {
+cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                           const nbk::ISrc* isrc) {
   if (n <= 0) return cudaSuccess;
+  const nbk::ISrc is = isrc ? *isrc : nbk::ISrc();
   NB_FP64_CASE(64, 32) NB_FP64_CASE(64, 64) NB_FP64_CASE(64, 128)
   NB_FP64_CASE(128, 32) NB_FP64_CASE(128, 64) NB_FP64_CASE(128, 128)
   NB_FP64_CASE(256, 32) NB_FP64_CASE(256, 64) NB_FP64_CASE(256, 128)

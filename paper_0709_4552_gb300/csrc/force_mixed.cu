@@ -25,14 +25,14 @@ __global__ void NB_MIXED_BOUNDS(NT, IPT) force_mixed_kernel(
     const float4* __restrict__ jA, const float4* __restrict__ jB, const float2* __restrict__ jC,
     int64_t n_j, const int32_t* __restrict__ list, int64_t n, int64_t tiles, float eps2,
     double* __restrict__ out, int64_t ostride, int finalize, const float4* __restrict__ tbox,
-    const int32_t* __restrict__ ord) {
+    const int32_t* __restrict__ ord, const nbk::ISrc is) {
   __shared__ __align__(16) nbk::MixedSmem<JT> sm;
   const int split = blockIdx.y;
   const int64_t jlo = nbk::split_begin(split, gridDim.y, tiles) * JT;
   const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * (NT * IPT),
-                               eps2, o, ostride, finalize != 0, tbox, ord);
+                               eps2, o, ostride, finalize != 0, tbox, ord, 0, nbk::FusedArgs(), is);
 }
 
 // the same item with on-the-fly prediction of the j-tiles from the j-memory
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(NT) force_mixed_fused_kernel(
 
 template <int NT, int IPT, int JT>
 cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg, float eps2,
-                   const int32_t* ord) {
+                   const int32_t* ord, const nbk::ISrc& is) {
   static int per_sm = 0;  // resident CTAs per SM of this instantiation
   if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_mixed_kernel<NT, IPT, JT>, NT,
                                                                    0) != cudaSuccess)
@@ -82,7 +82,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
   // context asks for double-single differences on every tile)
   const float4* tbox = (c->perm_valid && c->far_tiles) ? c->tbox : nullptr;
   force_mixed_kernel<NT, IPT, JT><<<grid, NT, 0, c->stream>>>(c->jA, c->jB, c->jC, n_j, d_list, n, tiles,
-                                                              eps2, out, ostride, fin ? 1 : 0, tbox, ord);
+                                                              eps2, out, ostride, fin ? 1 : 0, tbox, ord, is);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
   return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
@@ -131,11 +131,12 @@ bool nb_mixed_supported(const nb_tuning& t) {
 
 #define NB_MIXED_CASE(NT_, IPT_, JT_)                            \
   if (cfg.threads == NT_ && cfg.ipt == IPT_ && cfg.jtile == JT_) \
-    return launch<NT_, IPT_, JT_>(c, d_list, n, cfg, eps2, ord);
+    return launch<NT_, IPT_, JT_>(c, d_list, n, cfg, eps2, ord, is);
 
 cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
-                            const int32_t* ord) {
+                            const int32_t* ord, const nbk::ISrc* isrc) {
   if (n <= 0) return cudaSuccess;
+  const nbk::ISrc is = isrc ? *isrc : nbk::ISrc();
   const float eps2 = (float)(c->eps * c->eps);
 #define NB_MIXED_JT(NT_, IPT_) NB_MIXED_CASE(NT_, IPT_, 64) NB_MIXED_CASE(NT_, IPT_, 128) NB_MIXED_CASE(NT_, IPT_, 256)
 #define NB_MIXED_IPT(NT_) NB_MIXED_JT(NT_, 1) NB_MIXED_JT(NT_, 2) NB_MIXED_JT(NT_, 4)

@@ -136,6 +136,14 @@ struct nb_ctx {
   int64_t jpred_max_n;
   bool plist_valid;          // the last force call predicted its own list (nb_compute_forces_at)
   double t_plist;
+  // i-particles held elsewhere (the ring algorithm's visiting block, exchange.cu),
+  // capacity ext_cap, allocated on first use
+  double *ext_x, *ext_v;     // SoA [3][ext_cap]
+  float4 *ext_A, *ext_B;
+  float2* ext_C;
+  int32_t *ext_self, *ext_ident;
+  int64_t* ext_gid;          // staged global ids of a host block
+  int64_t ext_cap;
   // tuning
   nb_tuning tune_override;   // all-zero = automatic
   nb_tune_entry tune_table[NB_TUNE_MAX];
@@ -177,12 +185,31 @@ cudaError_t nb_launch_jm_host_side(nb_ctx* c, const int32_t* d_list, int64_t n, 
 // make the j-memory current (allocate, rebuild when the state changed)
 int nb_jm_ensure(nb_ctx* c);
 
+// ---- exchange between ranks (exchange.cu) ----------------------------------
+// dst[k][r] = src[r][slots[k]] (rows 1 or 3) and the reverse
+cudaError_t nb_launch_gather_slots(nb_ctx* c, const int32_t* slots, int64_t n, const double* src, int rows,
+                                   double* dst);
+cudaError_t nb_launch_scatter_slots(nb_ctx* c, const int32_t* slots, int64_t n, const double* src, int rows,
+                                    double* dst);
+cudaError_t nb_ext_reserve(nb_ctx* c, int64_t n);  // i-arrays for n particles held elsewhere
+// the block (device AoS xi, vi [n][3]; gid nullable) into the i-arrays
+cudaError_t nb_launch_ext_prepare(nb_ctx* c, int64_t n, const double* xi, const double* vi, const int64_t* gid,
+                                  int64_t base);
+cudaError_t nb_forces_ext(nb_ctx* c, int64_t n, const nb_tuning& cfg);  // forces on the i-arrays -> F
+// F rows [0, n) to device outputs (any NULL), added on when accumulate
+cudaError_t nb_launch_forces_out(nb_ctx* c, int64_t n, double* acc, double* jerk, double* pot, int accumulate);
+
 // ---- launchers (force_fp64.cu / force_mixed.cu) ----------------------------
-// forces on the list d_list[0..n) from all N j; results to c->F
-cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg);
+namespace nbk {
+struct ISrc;  // i-particles held elsewhere (force_common.cuh)
+}
+// forces on the list d_list[0..n) from all N j; results to c->F.  isrc
+// (optional): the i-particles come from those arrays instead of the j-store
+cudaError_t nb_forces_fp64(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
+                           const nbk::ISrc* isrc = nullptr);
 // ord (optional): processing order of the list positions (spatial order)
 cudaError_t nb_forces_mixed(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
-                            const int32_t* ord = nullptr);
+                            const int32_t* ord = nullptr, const nbk::ISrc* isrc = nullptr);
 // the mixed item with the j-tiles predicted to T from the j-memory
 cudaError_t nb_forces_mixed_fused(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg,
                                   const int32_t* ord, double T, const float4* boxes);

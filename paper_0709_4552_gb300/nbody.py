@@ -30,7 +30,8 @@ NB_JPREDICT_AUTO = -1
 EXPORTS = (
     "nb_create", "nb_destroy", "nb_set_params", "nb_get_params", "nb_default_params", "nb_set_precision",
     "nb_set_j_particles", "nb_set_n", "nb_get_n", "nb_get_particles", "nb_next_block", "nb_predict",
-    "nb_compute_forces", "nb_compute_forces_at", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
+    "nb_compute_forces", "nb_compute_forces_at", "nb_get_particles_idx", "nb_set_particles_idx",
+    "nb_get_predicted", "nb_forces_on", "nb_set_forces", "nb_set_initial_forces", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
     "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
@@ -81,6 +82,12 @@ def lib():
         "nb_compute_forces": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _int]),
         "nb_compute_forces_at": (_int, [_vp, _d, _vp, _i64, _vp, _vp, _vp, _int]),
         "nb_set_jpredict": (_int, [_vp, _i64]),
+        "nb_get_particles_idx": (_int, [_vp, _vp, _i64] + [_vp] * 8 + [_int]),
+        "nb_set_particles_idx": (_int, [_vp, _vp, _i64] + [_vp] * 8 + [_int]),
+        "nb_get_predicted": (_int, [_vp, _vp, _i64, _vp, _vp, _int]),
+        "nb_forces_on": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _int, _int]),
+        "nb_set_forces": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _int]),
+        "nb_set_initial_forces": (_int, [_vp, _vp, _vp, _vp, _int]),
         "nb_get_jpredict": (_int, [_vp, _pi64]),
         "nb_correct": (_int, [_vp, _vp, _i64, _d, _int]),
         "nb_initial_forces_and_dt": (_int, [_vp]),
@@ -290,6 +297,70 @@ def nb_compute_forces_at(ctx, t, i_idx, acc=None, jerk=None, pot=None):
     if ret:
         return keep[1], keep[2], keep[3]
     return acc, jerk, pot
+
+
+_STATE_KEYS = ("m", "x", "v", "a", "jerk", "pot", "t", "dt")
+_STATE_SHAPE = dict(m=(), x=(3,), v=(3,), a=(3,), jerk=(3,), pot=(), t=(), dt=())
+
+
+def nb_get_particles_idx(ctx, idx, out=None, keys=_STATE_KEYS):
+    """Particles idx (ascending) of the state, list order: a dict of host
+    arrays for `keys`, or fills `out` (arrays/tensors; missing keys skipped)."""
+    n = int(idx.shape[0])
+    if out is None:
+        out = {k: np.empty((n,) + _STATE_SHAPE[k]) for k in keys}
+    kind, p, keep = _marshal([idx] + [out.get(k) for k in _STATE_KEYS], [np.int32] + [np.float64] * 8)
+    _check(lib().nb_get_particles_idx(ctx, p[0], n, *p[1:], kind), "nb_get_particles_idx")
+    for k, kp in zip(_STATE_KEYS, keep[1:]):
+        if k in out and isinstance(kp, np.ndarray) and kp is not out[k]:
+            out[k][...] = kp
+    return out
+
+
+def nb_set_particles_idx(ctx, idx, values):
+    """Write particles idx (ascending) from a dict of list-ordered arrays
+    (keys of m, x, v, a, jerk, pot, t, dt; missing keys stay unchanged)."""
+    n = int(idx.shape[0])
+    kind, p, keep = _marshal([idx] + [values.get(k) for k in _STATE_KEYS], [np.int32] + [np.float64] * 8)
+    _check(lib().nb_set_particles_idx(ctx, p[0], n, *p[1:], kind), "nb_set_particles_idx")
+    del keep
+
+
+def nb_get_predicted(ctx, idx, xp=None, vp=None):
+    n = int(idx.shape[0])
+    if xp is None and vp is None and type(idx).__module__ != "torch":
+        xp, vp = np.empty((n, 3)), np.empty((n, 3))
+    kind, p, keep = _marshal([idx, xp, vp], [np.int32, np.float64, np.float64])
+    _check(lib().nb_get_predicted(ctx, p[0], n, p[1], p[2], kind), "nb_get_predicted")
+    return (keep[1] if isinstance(keep[1], np.ndarray) else xp), (keep[2] if isinstance(keep[2], np.ndarray) else vp)
+
+
+def nb_forces_on(ctx, xi, vi, gid=None, gid_base=0, acc=None, jerk=None, pot=None, accumulate=False):
+    """Forces on particles held elsewhere (predicted xi, vi [n,3]) from this
+    context's j-particles; gid (int64, nullable) excludes the self pair.
+    Host inputs without outputs return new arrays."""
+    n = int(xi.shape[0])
+    if acc is None and jerk is None and pot is None and type(xi).__module__ != "torch":
+        acc, jerk, pot = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    kind, p, keep = _marshal([xi, vi, gid, acc, jerk, pot],
+                             [np.float64, np.float64, np.int64, np.float64, np.float64, np.float64])
+    _check(lib().nb_forces_on(ctx, n, p[0], p[1], p[2], int(gid_base), p[3], p[4], p[5], int(bool(accumulate)),
+                              kind), "nb_forces_on")
+    for dst, kp in ((acc, keep[3]), (jerk, keep[4]), (pot, keep[5])):
+        if isinstance(dst, np.ndarray) and isinstance(kp, np.ndarray) and kp is not dst:
+            dst[...] = kp
+    return acc, jerk, pot
+
+
+def nb_set_forces(ctx, idx, acc, jerk, pot):
+    n = int(idx.shape[0])
+    kind, p, keep = _marshal([idx, acc, jerk, pot], [np.int32, np.float64, np.float64, np.float64])
+    _check(lib().nb_set_forces(ctx, p[0], n, p[1], p[2], p[3], kind), "nb_set_forces")
+
+
+def nb_set_initial_forces(ctx, acc, jerk, pot):
+    kind, p, keep = _marshal([acc, jerk, pot], [np.float64] * 3)
+    _check(lib().nb_set_initial_forces(ctx, p[0], p[1], p[2], kind), "nb_set_initial_forces")
 
 
 def nb_set_jpredict(ctx, max_n):
