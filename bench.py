@@ -66,7 +66,8 @@ def parse():
                     choices=["c3", "c2", "c4", "c5", "tapp", "c3sweep", "c4init"],
                     help="c3 (default): the timed benchmark; c2/c4/c5: long integrations; tapp: time per "
                          "N-body time unit vs N and the per-task model; one JSON line each")
-    ap.add_argument("--tune-file", default="", help="c4: save the autotuned table to this JSON file")
+    ap.add_argument("--tune-file", default="",
+                    help="c3sweep / c4: save the autotuned table to this JSON file (c3sweep adds to it)")
     ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
     return ap.parse_args()
 
@@ -449,13 +450,27 @@ def run_integration(args):
             pos = inputs.sample_indices(n, min(n, 1024), 2003)
             ref = oracle.forces(m, xp, vp, eps, idx=act[pos].astype(np.int64), compensated=True)
             row = {"n_active": n}
-            for prec, name in ((nb.NB_MIXED, "mixed"), (nb.NB_MIXED, "mixed_onthefly"), (nb.NB_FP64, "fp64")):
+            for prec, name in ((nb.NB_MIXED, "mixed"), (nb.NB_MIXED, "mixed_autotuned"),
+                               (nb.NB_MIXED, "mixed_onthefly"), (nb.NB_FP64, "fp64")):
                 if prec == nb.NB_FP64 and n > 65536:
                     continue  # 1.1e12 FP64 interactions take over a minute; the sample covers accuracy
+                if name == "mixed_autotuned" and n > 65536:
+                    continue  # the tuner's ~80 trial launches of 0.9 s each at n = N
                 s = nb.NBody(N, prec, 0, stream=torch.cuda.current_stream())
                 s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
                 s.set_j_particles(0, *state)
                 d_act = torch.from_numpy(act).cuda()
+                tuned = None
+                if name == "mixed_autotuned":
+                    # nb_autotune on this block (its trial launches use the first n particles of
+                    # the same state), then the same timed calls take the tuned launch; with
+                    # --tune-file the table collects every n's entry
+                    if args.tune_file and os.path.exists(args.tune_file):
+                        s.tune_load(args.tune_file)
+                    s.predict(T)
+                    tuned = s.autotune(n)
+                    if args.tune_file:
+                        s.tune_save(args.tune_file)
                 A = torch.empty((n, 3), dtype=torch.float64, device="cuda")
                 J = torch.empty_like(A)
                 P = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -494,6 +509,8 @@ def run_integration(args):
                              "acc_median": float(np.median(ea)), "acc_max": float(ea.max()),
                              "jerk_median": float(np.median(ej)), "jerk_max": float(ej.max()),
                              "pot_max": float(ep.max())}
+                if tuned is not None:
+                    row[name]["tuning"] = tuned
             row["onthefly_speedup"] = row["mixed"]["ms_total"] / row["mixed_onthefly"]["ms_total"]
             res.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)

@@ -1063,8 +1063,11 @@ int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_ti
         // smaller and a larger explicit one
         const int guess = nb_auto_split(c, n, cfg, 4);
         const int splits[] = {0, std::max(1, guess / 2), guess * 2};
+        // explicit splits beyond the partial-sum scratch (or the supported
+        // maximum) cannot launch: not candidates
+        const int64_t cap = std::min<int64_t>(4096, c->part_elems / (7 * (((n + 31) / 32) * 32)));
         for (int si = 0; si < 3; ++si) {
-          if (si > 0 && (guess == 1 || splits[si] == splits[si - 1])) continue;
+          if (si > 0 && (guess == 1 || splits[si] == splits[si - 1] || splits[si] > cap)) continue;
           nb_tuning t = cfg;
           t.nsplit = splits[si];
           c->tune_override = t;

@@ -144,6 +144,100 @@ __device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, 
   dt[i] = dnew;
 }
 
+// The same correction spread over four lanes of a warp: lane `sub` < 3 of
+// the group takes component `sub` (the same FP64 operations in the same order
+// as correct_row), the squared norms are gathered by shuffles and summed in
+// component order on every lane, lanes 0-3 take one square root each, and
+// lane 0 applies the step rule.  The result is correct_row's, bit for bit;
+// the dependent FP64 chain is about a third as long, which matters where one
+// particle's correction is the critical path of a block step.
+//
+// Every lane of the warp must call this with the same control flow: the
+// shuffles use the full mask and are taken unconditionally.  `base` is the
+// warp lane of the group's lane 0; `write` says whether this group's row is
+// real (lanes of groups without a row, and lanes sub >= 4, compute on a
+// valid row and write nothing).
+__device__ __forceinline__ void correct_row_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
+                                                   double eta, double dt_min, double dt_max, double* __restrict__ x,
+                                                   double* __restrict__ v, double* __restrict__ a,
+                                                   double* __restrict__ jk, double* __restrict__ pot,
+                                                   double* __restrict__ ti, double* __restrict__ dt,
+                                                   const double* __restrict__ xp, const double* __restrict__ vp,
+                                                   nb_dev_status* __restrict__ st, int sub, int base, bool write) {
+  const double h = t - ti[i];
+  const double ih = div_pow2(1.0, h);
+  const double ih2 = ih * ih, ih3 = ih2 * ih;
+  const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};  // a1^2, j1^2, a2e^2, a3^2 of this lane's component
+  int fin = 1;
+  const int c = sub < 3 ? sub : 0;
+  {
+    const int64_t q = c * n_pad + i;
+    const double a0 = a[q], j0 = jk[q];
+    // (selects, not an index: f stays in registers)
+    const double a1 = c == 0 ? f[0] : (c == 1 ? f[1] : f[2]);
+    const double j1 = c == 0 ? f[3] : (c == 1 ? f[4] : f[5]);
+    const double da = a0 - a1;
+    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
+    const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
+    const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
+    const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+    const double a2e = a2 + a3 * h;
+    if (write && sub < 3) {
+      x[q] = x1;
+      v[q] = v1;
+      a[q] = a1;
+      jk[q] = j1;
+    }
+    sq[0] = a1 * a1;
+    sq[1] = j1 * j1;
+    sq[2] = a2e * a2e;
+    sq[3] = a3 * a3;
+    fin = (isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1)) ? 1 : 0;
+  }
+  // norms summed in component order on every lane (0 + x^2 + y^2 + z^2, as
+  // correct_row's running sums); every shuffle is taken by every lane
+  double nrm2[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const double s0 = __shfl_sync(0xffffffffu, sq[r], base);
+    const double s1 = __shfl_sync(0xffffffffu, sq[r], base + 1);
+    const double s2 = __shfl_sync(0xffffffffu, sq[r], base + 2);
+    nrm2[r] = ((0.0 + s0) + s1) + s2;
+  }
+  const int f0 = __shfl_sync(0xffffffffu, fin, base);
+  const int f1 = __shfl_sync(0xffffffffu, fin, base + 1);
+  const int f2 = __shfl_sync(0xffffffffu, fin, base + 2);
+  // one square root per lane, gathered on lane 0
+  const double mine = sub == 1 ? nrm2[1] : (sub == 2 ? nrm2[2] : (sub == 3 ? nrm2[3] : nrm2[0]));
+  const double root = sqrt(mine);
+  const double na = __shfl_sync(0xffffffffu, root, base);
+  const double nj = __shfl_sync(0xffffffffu, root, base + 1);
+  const double n2 = __shfl_sync(0xffffffffu, root, base + 2);
+  const double n3 = __shfl_sync(0xffffffffu, root, base + 3);
+  if (!write || sub != 0) return;
+  const double p1 = f[6];
+  pot[i] = p1;
+  const double num = na * n2 + nj * nj;
+  const double den = nj * n3 + n2 * n2;
+  const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
+  if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
+  const double dt_old = dt[i];
+  const double cl = clamp_dt(pow2_floor(crit), dt_min, dt_max);
+  double dnew;
+  if (cl < dt_old) {
+    dnew = cl;
+  } else {
+    const double two = 2.0 * dt_old;
+    const double qq = div_pow2(t, two);  // exact: two is a power of two
+    dnew = (cl >= two && two <= dt_max && qq == floor(qq)) ? two : dt_old;
+  }
+  const bool finite = f0 && f1 && f2;
+  if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
+  ti[i] = t;
+  dt[i] = dnew;
+}
+
 // j-memory record of row i (the on-the-fly j prediction's input, Sec. 4.4
 // step 4; layout in force_common.cuh): double-single position and velocity,
 // a/2 and jerk/6 in FP32, the mass, and the reach Rd >= |v_c| dt + |a_c| dt^2/2

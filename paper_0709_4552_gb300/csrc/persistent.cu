@@ -347,9 +347,11 @@ __device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles
   // own list positions, up to 128 per round: L = 128 / P' threads per
   // position (P' = the round's positions rounded up to a power of two, at
   // least 4) sum its j-splits (lane l takes splits l, l + L, ... in order;
-  // a butterfly over the L lanes), and lane 0 of each group corrects it
-  // (step 5): one position per thread when the block is large, 32 lanes per
-  // position when it is small and the splits many
+  // a butterfly over the L lanes), and the group corrects it (step 5): lanes
+  // 0-3 together when it has at least four (the correction's FP64 chain is
+  // the critical path of a small block's step), else lane 0 alone: one
+  // position per thread when the block is large, 32 lanes per position when
+  // it is small and the splits many
   for (int k0 = 0; k0 < mycnt; k0 += kLT) {
     const int P = min(mycnt - k0, kLT);
     int Pp = 4;
@@ -360,7 +362,7 @@ __device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles
     const int64_t k = before + k0 + (have ? q : 0);
     double f[7];
     if (fin) {
-      if (have && l == 0)
+      if (have && l < 4)
 #pragma unroll
         for (int r = 0; r < 7; ++r) f[r] = p.F[r * p.n_pad + k];
     } else {
@@ -375,7 +377,17 @@ __device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles
         for (int r = 0; r < 7; ++r) f[r] += __shfl_xor_sync(0xffffffffu, f[r], o);
       f[6] = -f[6];
     }
-    if (have && l == 0) {
+    if (L >= 4) {
+      // every lane of the CTA takes this branch (L is uniform) and every
+      // shuffle inside; lanes without a row read a valid own row, write nothing
+      int64_t i = p.act[k];
+      i = i < r0 ? r0 : (i >= r1 ? r1 - 1 : i);  // own rows only
+      if (!(have && l < 4))
+#pragma unroll
+        for (int r = 0; r < 7; ++r) f[r] = 0.0;
+      nbh::correct_row_lanes4(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t, p.dt,
+                              p.xp, p.vp, p.st, l, (int)(threadIdx.x & 31) - l, have);
+    } else if (have && l == 0) {
       int64_t i = p.act[k];
       i = i < r0 ? r0 : (i >= r1 ? r1 - 1 : i);  // own rows only
       nbh::correct_row(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t, p.dt, p.xp,
@@ -542,7 +554,11 @@ int nb_integrate_persistent(nb_ctx* c, double t_end) {
     cudaGetLastError();
     return NB_ECUDA;
   }
-  const int G = std::min(c->sm_count * per_sm, kLMaxG);
+  // as many CTAs as fit, but for a small system no more than twice its row
+  // tiles (at least 32): the other CTAs would own no rows and take no force
+  // items of its small blocks, and each barrier waits for every CTA's arrival
+  const int64_t row_tiles = (c->n + kLT - 1) / kLT;
+  const int G = (int)std::min<int64_t>(std::min(c->sm_count * per_sm, kLMaxG), std::max<int64_t>(32, 2 * row_tiles));
   if (G > L->gmax) {
     if (L->smin) cudaFree(L->smin);
     if (L->scnt) cudaFree(L->scnt);

@@ -24,6 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -172,13 +173,24 @@ void nb_tune_store(nb_ctx* c, int kind, int64_t N, int64_t n, const nb_tuning& c
   e.n_hi = (int64_t)(n * fn) + 1;
   e.cfg = cfg;
   e.ms = ms;
+  // an entry of the same workload bin (its own n inside the new bin) is
+  // replaced; a neighbour whose bin merely overlaps keeps its range and the
+  // new bin stops at its edge, so that every (N, n) has one entry
   int slot = -1;
   for (int i = 0; i < c->tune_count; ++i) {
     const nb_tune_entry& o = c->tune_table[i];
-    if (o.kind == kind && o.precision == e.precision && o.N_lo < e.N_hi && e.N_lo < o.N_hi && o.n_lo < e.n_hi &&
-        e.n_lo < o.n_hi)
+    if (o.kind != kind || o.precision != e.precision || o.N_hi <= e.N_lo || e.N_hi <= o.N_lo) continue;
+    if (o.n_hi <= e.n_lo || e.n_hi <= o.n_lo) continue;
+    const double oc = sqrt((double)o.n_lo * (double)o.n_hi);  // the n it was tuned at
+    if (n >= o.n_lo && n < o.n_hi && oc >= e.n_lo && oc < e.n_hi) {
       slot = i;
+    } else if (o.n_hi <= n) {
+      e.n_lo = std::max(e.n_lo, o.n_hi);
+    } else {
+      e.n_hi = std::min(e.n_hi, o.n_lo);
+    }
   }
+  if (e.n_hi <= e.n_lo) return;  // squeezed out by its neighbours
   if (slot < 0) slot = c->tune_count < NB_TUNE_MAX ? c->tune_count++ : NB_TUNE_MAX - 1;
   c->tune_table[slot] = e;
 }

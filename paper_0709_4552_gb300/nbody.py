@@ -17,6 +17,10 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbody.so")
+# the autotuner's table measured on a GB300 (152 SMs), shipped with the
+# package; contexts load it through NB_TUNE_FILE unless the caller set that
+# (the library refuses a table measured on a GPU with another SM count)
+DEFAULT_TUNE_FILE = os.path.join(HERE, "tuning", "gb300_152sm.json")
 
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ENUMERIC, NB_EDTMIN, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 NB_FP64, NB_MIXED = 0, 1
@@ -65,6 +69,8 @@ def lib():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"{LIB_PATH} is missing: build it with "
                            "`python -m paper_0709_4552_gb300.build` (needs nvcc); there is no fallback")
+    if "NB_TUNE_FILE" not in os.environ and os.path.exists(DEFAULT_TUNE_FILE):
+        os.environ["NB_TUNE_FILE"] = DEFAULT_TUNE_FILE
     L = ctypes.CDLL(LIB_PATH)
     sig = {
         "nb_create": (_int, [ctypes.POINTER(_vp), _i64, _int, _int, _vp]),

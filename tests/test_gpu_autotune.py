@@ -35,7 +35,8 @@ def _ens(nb, prec, off, m, x, v, eps, t_end):
     return e
 
 
-def test_table_file_round_trip(nbl, tmp_path):
+def test_table_file_round_trip(nbl, tmp_path, monkeypatch):
+    monkeypatch.setenv("NB_TUNE_FILE", "")   # no shipped table: the contexts start empty
     N = 20000
     m, x, v = inputs.plummer(N, 51)
     path1, path2 = str(tmp_path / "t1.json"), str(tmp_path / "t2.json")
@@ -59,15 +60,13 @@ def test_table_file_round_trip(nbl, tmp_path):
         nbl.nb_tune_save(s.ctx, path2)
     assert json.load(open(path2)) == doc
     # the environment variable is read when a context is made
-    os.environ["NB_TUNE_FILE"] = path1
-    try:
-        with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
-            assert s.tune_count() == 1
-    finally:
-        del os.environ["NB_TUNE_FILE"]
+    monkeypatch.setenv("NB_TUNE_FILE", path1)
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        assert s.tune_count() == 1
 
 
-def test_table_refuses_foreign_or_broken_files(nbl, tmp_path):
+def test_table_refuses_foreign_or_broken_files(nbl, tmp_path, monkeypatch):
+    monkeypatch.setenv("NB_TUNE_FILE", "")
     with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
         good = {"format": "libnbody tuning table 1", "device": "x", "sm_count": 0, "entries": []}
         bad_sm = str(tmp_path / "sm.json")
@@ -81,11 +80,22 @@ def test_table_refuses_foreign_or_broken_files(nbl, tmp_path):
         assert s.tune_count() == 0
 
 
+def test_shipped_table_loads(nbl):
+    # the package's GB300 table (when present) is what a new context starts from
+    from paper_0709_4552_gb300 import nbody
+    if not os.path.exists(nbody.DEFAULT_TUNE_FILE) or os.environ.get("NB_TUNE_FILE") != nbody.DEFAULT_TUNE_FILE:
+        pytest.skip("no shipped table in use")
+    doc = json.load(open(nbody.DEFAULT_TUNE_FILE))
+    with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
+        assert s.tune_count() == len(doc["entries"])
+
+
 def test_ensemble_autotune_restores_the_state(nbl):
     sizes = [300, 90, 700, 128, 1000]
     off, m, x, v, eps = _ensemble_ics(sizes, 710)
     N = int(off[-1])
     with _ens(nbl, nbl.NB_MIXED, off, m, x, v, eps, 2.0 ** -5) as e:
+        e.tune_clear()
         before = e.get_particles(0, N)
         c0 = e.get_counters()
         res = e.autotune(8)
