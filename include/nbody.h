@@ -311,17 +311,29 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  *                       whole run (a few CTAs per SM, three grid barriers per
  *                       block step, each wait bounded), for systems whose
  *                       block steps are latency-bound: N <= NB_PERSISTENT_MAX_N.
+ *   NB_LOOP_CLUSTER     one thread-block cluster (16 CTAs, one per SM; 8 where
+ *                       the GPU cannot co-schedule 16) for the whole run, the
+ *                       ring algorithm of Sec. 4.3 on one chip: each CTA holds
+ *                       N/16 particles in shared memory, predicted on the fly
+ *                       (Sec. 4.4 step 4), the active block visits every CTA
+ *                       through distributed shared memory, and the cluster's
+ *                       hardware barrier separates the phases (three per
+ *                       step; no spin wait).  Mixed path only, N <=
+ *                       NB_CLUSTER_MAX_N (8192 on an 8-CTA cluster).
  * All three take the same block steps with the same per-particle arithmetic;
  * sums over j-splits may group differently.  The mixed path renews its
  * spatial order between launches (graph and persistent loops run segments of
  * at most the sort interval).  Errors: NB_EINVAL (t_end, loop, N too large
  * for the persistent loop), NB_ENUMERIC, NB_ETIMEOUT (a bounded device wait
- * gave up; the state is then undefined), NB_ECUDA.
+ * gave up; the state is then undefined), NB_ECUDA.  NB_LOOP_CLUSTER: NB_EINVAL
+ * also for the FP64 path or N beyond what the cluster holds.
  */
 #define NB_LOOP_HOST        0
 #define NB_LOOP_GRAPH       1
 #define NB_LOOP_PERSISTENT  2
+#define NB_LOOP_CLUSTER     3
 #define NB_PERSISTENT_MAX_N 65536
+#define NB_CLUSTER_MAX_N    16384
 int nb_integrate(nb_ctx* ctx, double t_end, int loop);
 
 /*

@@ -458,6 +458,7 @@ void nb_destroy(nb_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   nb_ensemble_free(c);
   nb_persistent_free(c);
+  nb_cluster_free(c);
   free_ctx(c);
 }
 
@@ -940,10 +941,13 @@ int nb_integrate(nb_ctx* c, double t_end, int loop) {
   NB_SINGLE(c);
   if (c->n <= 0) return fail(c, NB_ESTATE);
   if (!(t_end > 0.0) || !isfinite(t_end) || fmod(t_end, c->dt_max) != 0.0) return fail(c, NB_EINVAL);
-  if (loop != NB_LOOP_HOST && loop != NB_LOOP_GRAPH && loop != NB_LOOP_PERSISTENT) return fail(c, NB_EINVAL);
+  if (loop != NB_LOOP_HOST && loop != NB_LOOP_GRAPH && loop != NB_LOOP_PERSISTENT && loop != NB_LOOP_CLUSTER)
+    return fail(c, NB_EINVAL);
   if (loop == NB_LOOP_PERSISTENT && c->n > NB_PERSISTENT_MAX_N) return fail(c, NB_EINVAL);
+  if (loop == NB_LOOP_CLUSTER && (c->n > NB_CLUSTER_MAX_N || c->precision != NB_MIXED)) return fail(c, NB_EINVAL);
   int r = loop == NB_LOOP_GRAPH        ? nb_integrate_graph(c, t_end)
           : loop == NB_LOOP_PERSISTENT ? nb_integrate_persistent(c, t_end)
+          : loop == NB_LOOP_CLUSTER    ? nb_integrate_cluster(c, t_end)
                                        : integrate_host_loop(c, t_end);
   if (loop != NB_LOOP_HOST) c->state_ver++;  // device-driven corrections (the host loop counts its own)
   c->plist_valid = false;

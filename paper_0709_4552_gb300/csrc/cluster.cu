@@ -1,0 +1,482 @@
+// cluster.cu -- the block-step loop of one small system (mixed path) on one
+// thread-block cluster: the paper's ring algorithm (Sec. 4.3) on one chip.
+//
+// The C CTAs of a cluster (16 where the GPU can co-schedule them, else 8; one
+// per SM) each own a contiguous slice of at most 1024 rows -- their "N/p
+// particles" -- and keep it in shared memory, predicted to each block time on
+// the fly from the j-memory (the GRAPE-style double-single records of
+// onboard.cu, Sec. 4.4 step 4).  Per block step (Sec. 4.1 steps 2-5):
+//   A  every CTA has published the minimum of t_i + dt_i over its rows and
+//      how many rows reach it; each reads all C pairs from the others' shared
+//      memory (distributed shared memory), takes the block time and its
+//      offset in the active list, lists its active rows, predicts them in
+//      FP64 (step 3; kept for the corrector) and as double-single i data, and
+//      predicts its j rows on the fly;
+//   B  the active block, in groups of 256: each CTA gathers the group's i data
+//      from the owners' shared memory and sums the forces of its own j rows
+//      on it (step 4, Eq. 3: FP32 pairwise arithmetic on double-single
+//      differences, per-chunk FP32 sums folded into double-single, the self
+//      pair excluded by row);
+//   C  each owner adds the C partial sums of its particles in CTA order and
+//      corrects them (step 5; the four-lane corrector of hermite.cuh), then
+//      rewrites their j-memory records and publishes its next minimum.
+// The barriers are the cluster's hardware barrier (no spin loop anywhere);
+// every CTA reads the same published values, so every CTA takes the same
+// decisions and leaves the loop at the same step.  Nothing leaves the chip
+// but the state each owner writes back.
+#include <cooperative_groups.h>
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "force_common.cuh"
+#include "hermite.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kCT = 256;       // threads per CTA
+constexpr int kCRows = 1024;   // rows per CTA at most
+constexpr int kGI = 256;       // active particles per force group
+constexpr int kChunk = 128;    // j per FP32 partial sum before the double-single fold
+constexpr int kMaxC = 16;      // CTAs per cluster at most
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;
+
+struct ClusterCtl {
+  long long steps;
+  long long interactions;
+};
+
+struct ClusterArgs {
+  int64_t N, n_pad;
+  float eps2f;
+  double eta, dt_min, dt_max, t_end;
+  long long max_steps;
+  const double* m;
+  double *x, *v, *a, *jk, *pot, *t, *dt;
+  double *xp, *vp;
+  float4* jm;
+  ClusterCtl* ctl;
+  nb_dev_status* st;
+};
+
+struct CSmem {
+  // own rows predicted to the block time (double-single positions, FP32 v, m)
+  float jxh[kCRows], jyh[kCRows], jzh[kCRows], jxl[kCRows], jyl[kCRows], jzl[kCRows];
+  float jvx[kCRows], jvy[kCRows], jvz[kCRows], jms[kCRows];
+  // own active particles in list order: predicted i data and their rows
+  float ixh[kCRows], iyh[kCRows], izh[kCRows], ixl[kCRows], iyl[kCRows], izl[kCRows];
+  float ivx[kCRows], ivy[kCRows], ivz[kCRows];
+  int32_t irow[kCRows];
+  // the force group's i data, gathered from the owners
+  float gxh[kGI], gyh[kGI], gzh[kGI], gxl[kGI], gyl[kGI], gzl[kGI], gvx[kGI], gvy[kGI], gvz[kGI];
+  int32_t grow[kGI];
+  // this CTA's partial sums on the group (read by the owners)
+  double part[7][kGI];
+  // the owner's sums of its particles of the group (all CTAs' partials)
+  double fsum[7][kGI];
+  // published: minimum of t_i + dt_i over own rows (bit pattern), rows at it
+  unsigned long long pmin;
+  int pcnt;
+  // every CTA's offset and count in the active list (read at barrier A)
+  int cbefore[kMaxC], cmine[kMaxC];
+  double tn;
+  long long total;
+  unsigned long long wmin[kCT / 32];
+  int wcnt[kCT / 32];
+};
+
+// minimum of t_i + dt_i over own rows and the rows at it -> s.pmin, s.pcnt
+__device__ void publish(const ClusterArgs& p, CSmem& s, int64_t r0, int nr) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  unsigned long long best = kInfBits;
+  for (int q = tid; q < nr; q += kCT) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]);
+    best = b < best ? b : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, best, o);
+    best = u < best ? u : best;
+  }
+  if (lane == 0) s.wmin[w] = best;
+  __syncthreads();
+  best = kInfBits;
+  for (int k = 0; k < kCT / 32; ++k) best = s.wmin[k] < best ? s.wmin[k] : best;
+  int cnt = 0;
+  for (int q = tid; q < nr; q += kCT)
+    cnt += (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == best;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s.wcnt[w] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int c = 0;
+    for (int k = 0; k < kCT / 32; ++k) c += s.wcnt[k];
+    s.pmin = best;
+    s.pcnt = c;
+  }
+}
+
+// own rows at the block time, ascending, into s.irow (each thread scans a
+// contiguous run of rows; a block scan places the runs in order)
+__device__ void list_rows(const ClusterArgs& p, CSmem& s, int64_t r0, int nr, unsigned long long tnb) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int W = (nr + kCT - 1) / kCT;
+  const int q0 = min(tid * W, nr), q1 = min(q0 + W, nr);
+  int cnt = 0;
+  for (int q = q0; q < q1; ++q) cnt += (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == tnb;
+  int inc = cnt;  // inclusive warp scan
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) s.wcnt[w] = inc;
+  __syncthreads();
+  int base = 0;
+  for (int k = 0; k < w; ++k) base += s.wcnt[k];
+  int at = base + inc - cnt;
+  for (int q = q0; q < q1; ++q)
+    if ((unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == tnb) s.irow[at++] = (int32_t)(r0 + q);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void split_ds(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+__global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CSmem& s = *reinterpret_cast<CSmem*>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int me = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int64_t N = p.N;
+  const int64_t R = (N + C - 1) / C;  // rows per CTA (<= kCRows, checked by the host)
+  const int64_t r0 = min((int64_t)me * R, N);
+  const int nr = (int)(min(r0 + R, N) - r0);
+  long long steps = 0;
+
+  publish(p, s, r0, nr);
+  for (;;) {
+    cl.sync();  // A: every CTA's minimum and count are published
+    if (tid < 32) {  // lane c reads CTA c's pair; the minimum and the offsets by shuffles
+      const unsigned long long pm = tid < C ? *cl.map_shared_rank(&s.pmin, tid) : kInfBits;
+      const int pc = tid < C ? *cl.map_shared_rank(&s.pcnt, tid) : 0;
+      unsigned long long tb = pm;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, tb, o);
+        tb = u < tb ? u : tb;
+      }
+      const int k = (tid < C && pm == tb) ? pc : 0;
+      int inc = k;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (tid >= o) inc += u;
+      }
+      if (tid < C) {
+        s.cbefore[tid] = inc - k;
+        s.cmine[tid] = k;
+      }
+      if (tid == 31) {
+        s.tn = __longlong_as_double((long long)tb);
+        s.total = inc;
+      }
+    }
+    __syncthreads();
+    const double tn = s.tn;
+    const long long n = s.total;
+    if (!isfinite(tn) || n <= 0) {  // no particle has a finite next time
+      if (me == 0 && tid == 0) atomicOr(&p.st->flags, NB_ST_NUMERIC);
+      break;
+    }
+    if (tn > p.t_end) break;  // every particle has reached t_end
+    if (steps >= p.max_steps) {
+      if (me == 0 && tid == 0) atomicOr(&p.st->flags, NB_ST_TIMEOUT);
+      break;
+    }
+    const int mine = s.cmine[me], before = s.cbefore[me];
+    const unsigned long long tnb = (unsigned long long)__double_as_longlong(tn);
+    list_rows(p, s, r0, nr, tnb);
+    // own active particles: FP64 prediction (step 3) kept for the corrector,
+    // double-single i data for the forces
+    for (int k = tid; k < mine; k += kCT) {
+      const int64_t row = s.irow[k];
+      double px[3], pv[3];
+      nbh::taylor(row, p.n_pad, tn - p.t[row], p.x, p.v, p.a, p.jk, px, pv);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        p.xp[d * p.n_pad + row] = px[d];
+        p.vp[d * p.n_pad + row] = pv[d];
+      }
+      split_ds(px[0], s.ixh[k], s.ixl[k]);
+      split_ds(px[1], s.iyh[k], s.iyl[k]);
+      split_ds(px[2], s.izh[k], s.izl[k]);
+      s.ivx[k] = __double2float_rn(pv[0]);
+      s.ivy[k] = __double2float_rn(pv[1]);
+      s.ivz[k] = __double2float_rn(pv[2]);
+    }
+    // own j rows predicted on the fly from the j-memory (Sec. 4.4 step 4)
+    for (int q = tid; q < nr; q += kCT) {
+      const int64_t row = r0 + q;
+      const float4 R0 = p.jm[row], R1 = p.jm[p.n_pad + row], R2 = p.jm[2 * p.n_pad + row],
+                   R3 = p.jm[3 * p.n_pad + row], R4 = p.jm[4 * p.n_pad + row];
+      const float h = __double2float_rn(tn - p.t[row]);
+      const float h2 = 2.0f * h, h15 = 1.5f * h;
+      float hi, lo, vv;
+      nbk::ds_predict(R0.x, R1.x, R2.x, R3.x, R4.x, R2.w, h, h2, h15, hi, lo, vv);
+      s.jxh[q] = hi; s.jxl[q] = lo; s.jvx[q] = vv;
+      nbk::ds_predict(R0.y, R1.y, R2.y, R3.y, R4.y, R3.w, h, h2, h15, hi, lo, vv);
+      s.jyh[q] = hi; s.jyl[q] = lo; s.jvy[q] = vv;
+      nbk::ds_predict(R0.z, R1.z, R2.z, R3.z, R4.z, R4.w, h, h2, h15, hi, lo, vv);
+      s.jzh[q] = hi; s.jzl[q] = lo; s.jvz[q] = vv;
+      s.jms[q] = R0.w;
+    }
+    __syncthreads();
+    cl.sync();  // B: every CTA's i data is ready
+
+    for (long long g0 = 0; g0 < n; g0 += kGI) {
+      const int gn = (int)min((long long)kGI, n - g0);
+      // the group's i data from its owners' shared memory
+      for (int k = tid; k < gn; k += kCT) {
+        const int pos = (int)(g0 + k);
+        int c = 0;
+        while (c + 1 < C && s.cbefore[c + 1] <= pos) ++c;
+        const int a = pos - s.cbefore[c];
+        s.gxh[k] = *cl.map_shared_rank(&s.ixh[a], c);
+        s.gyh[k] = *cl.map_shared_rank(&s.iyh[a], c);
+        s.gzh[k] = *cl.map_shared_rank(&s.izh[a], c);
+        s.gxl[k] = *cl.map_shared_rank(&s.ixl[a], c);
+        s.gyl[k] = *cl.map_shared_rank(&s.iyl[a], c);
+        s.gzl[k] = *cl.map_shared_rank(&s.izl[a], c);
+        s.gvx[k] = *cl.map_shared_rank(&s.ivx[a], c);
+        s.gvy[k] = *cl.map_shared_rank(&s.ivy[a], c);
+        s.gvz[k] = *cl.map_shared_rank(&s.ivz[a], c);
+        s.grow[k] = *cl.map_shared_rank(&s.irow[a], c);
+      }
+      __syncthreads();
+      // own j rows on the group: P threads per particle (a power of two, at
+      // most 32, lanes of one warp), each over a contiguous part of the rows
+      int P = 32;
+      while (P > 1 && P * gn > kCT) P >>= 1;
+      const int i = tid / P, part = tid % P;
+      double f[7];
+      {
+        float hi7[7], lo7[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) hi7[c] = lo7[c] = 0.0f;
+        if (i < gn) {
+          const float xh = s.gxh[i], yh = s.gyh[i], zh = s.gzh[i], xl = s.gxl[i], yl = s.gyl[i], zl = s.gzl[i];
+          const float vx = s.gvx[i], vy = s.gvy[i], vz = s.gvz[i];
+          const int64_t self = (int64_t)s.grow[i] - r0;
+          const int q0 = (int)((int64_t)part * nr / P), q1 = (int)((int64_t)(part + 1) * nr / P);
+          for (int c0 = q0; c0 < q1; c0 += kChunk) {
+            const int c1 = min(c0 + kChunk, q1);
+            float pp[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) pp[c] = 0.0f;
+            for (int q = c0; q < c1; ++q) {
+              const float dx = (s.jxh[q] - xh) + (s.jxl[q] - xl);
+              const float dy = (s.jyh[q] - yh) + (s.jyl[q] - yl);
+              const float dz = (s.jzh[q] - zh) + (s.jzl[q] - zl);
+              const float wx = s.jvx[q] - vx, wy = s.jvy[q] - vy, wz = s.jvz[q] - vz;
+              const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, p.eps2f)));
+              const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+              float rinv = nb_rsqrt_approx(r2);
+              rinv = (q == self) ? 0.0f : rinv;  // the self pair, by row
+              const float rinv2 = rinv * rinv;
+              const float mr = s.jms[q] * rinv;
+              const float mr3 = mr * rinv2;
+              const float a3 = (rw * -3.0f) * rinv2;  // the jerk term formed before it is added
+              pp[6] += mr;
+              pp[0] = fmaf(mr3, dx, pp[0]);
+              pp[1] = fmaf(mr3, dy, pp[1]);
+              pp[2] = fmaf(mr3, dz, pp[2]);
+              pp[3] = fmaf(mr3, fmaf(a3, dx, wx), pp[3]);
+              pp[4] = fmaf(mr3, fmaf(a3, dy, wy), pp[4]);
+              pp[5] = fmaf(mr3, fmaf(a3, dz, wz), pp[5]);
+            }
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {  // double-single fold (Knuth's TwoSum)
+              const float a_ = hi7[c], b_ = pp[c];
+              const float sum = a_ + b_;
+              const float bb = sum - a_;
+              lo7[c] += (a_ - (sum - bb)) + (b_ - bb);
+              hi7[c] = sum;
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) f[c] = (double)hi7[c] + (double)lo7[c];
+      }
+      // the P parts of a particle, lanes of one warp: butterfly (every lane)
+      for (int o = P / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
+      if (i < gn && part == 0)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) s.part[c][i] = f[c];
+      __syncthreads();
+      cl.sync();  // C: every CTA's partial sums on the group are ready
+
+      // the owner's particles of this group: the C partials in CTA order, then
+      // the corrector on four lanes per particle (step 5)
+      const int lo_pos = max((int)g0, before), hi_pos = min((int)g0 + gn, before + mine);
+      const int own = hi_pos - lo_pos;  // CTA-uniform
+      // one thread per (particle, component): the C partials in CTA order
+      for (int e = tid; e < own * 7; e += kCT) {
+        const int k = lo_pos - (int)g0 + e / 7, c = e % 7;
+        double acc = 0.0;
+        for (int cc = 0; cc < C; ++cc) acc += *cl.map_shared_rank(&s.part[c][k], cc);
+        s.fsum[c][k] = c == 6 ? -acc : acc;
+      }
+      __syncthreads();
+      for (int k0 = 0; k0 < own; k0 += kCT / 4) {
+        const int sub = tid & 3;
+        const int pos = lo_pos + k0 + (tid >> 2);
+        const bool have = pos < hi_pos;
+        double fo[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) fo[c] = have ? s.fsum[c][pos - (int)g0] : 0.0;
+        const int64_t row = have ? (int64_t)s.irow[pos - before] : (int64_t)s.irow[lo_pos - before];
+        nbh::correct_row_lanes4(row, p.n_pad, tn, fo, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t,
+                                p.dt, p.xp, p.vp, p.st, sub, (tid & 31) - sub, have);
+        __syncwarp();
+        if (have && sub == 0) nbh::write_jm_record(row, N, p.n_pad, p.m, p.x, p.v, p.a, p.jk, p.dt, p.jm);
+      }
+      __syncthreads();
+      if (g0 + kGI < n) cl.sync();  // D: the partials are read before the next group's are written
+    }
+    ++steps;
+    if (me == 0 && tid == 0) {
+      p.ctl->steps = steps;
+      p.ctl->interactions += n * (long long)N;
+    }
+    __syncthreads();
+    publish(p, s, r0, nr);
+  }
+}
+
+struct CLoop {
+  ClusterCtl* ctl = nullptr;
+  int csize = 0;  // CTAs per cluster (0 = not yet chosen)
+};
+
+}  // namespace
+
+void nb_cluster_free(nb_ctx* c) {
+  CLoop* L = c ? static_cast<CLoop*>(c->cloop) : nullptr;
+  if (!L) return;
+  if (L->ctl) cudaFree(L->ctl);
+  delete L;
+  c->cloop = nullptr;
+}
+
+// CTAs per cluster this GPU co-schedules with the loop's shared memory: 16, else 8 (0 = none)
+int nb_cluster_size(nb_ctx* c) {
+  CLoop* L = static_cast<CLoop*>(c->cloop);
+  if (!L) {
+    L = new CLoop();
+    c->cloop = L;
+  }
+  if (L->csize) return L->csize;
+  const size_t smem = sizeof(CSmem);
+  if (cudaFuncSetAttribute(cluster_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(cluster_loop_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kCT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, cluster_loop_kernel, &cfg) == cudaSuccess && nclusters >= 1) {
+      L->csize = cs;
+      return cs;
+    }
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+int nb_integrate_cluster(nb_ctx* c, double t_end) {
+  if (c->precision != NB_MIXED || c->n_clusters > 0) return NB_EINVAL;
+  const int C = nb_cluster_size(c);
+  if (C < 1) return NB_ECUDA;
+  if (c->n > (int64_t)C * kCRows) return NB_EINVAL;
+  CLoop* L = static_cast<CLoop*>(c->cloop);
+  if (!L->ctl && cudaMalloc((void**)&L->ctl, sizeof(ClusterCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    return NB_ENOMEM;
+  }
+  const int rj = nb_jm_ensure(c);
+  if (rj != NB_OK) return rj;
+  ClusterArgs p;
+  memset(&p, 0, sizeof(p));
+  p.N = c->n;
+  p.n_pad = c->n_pad;
+  p.eps2f = (float)(c->eps * c->eps);
+  p.eta = c->eta;
+  p.dt_min = c->dt_min;
+  p.dt_max = c->dt_max;
+  p.t_end = t_end;
+  p.max_steps = std::min<long long>((long long)ceil(t_end / c->dt_min) + 2, 50000000LL);
+  p.m = c->m;
+  p.x = c->x;
+  p.v = c->v;
+  p.a = c->a;
+  p.jk = c->jk;
+  p.pot = c->pot;
+  p.t = c->t;
+  p.dt = c->dt;
+  p.xp = c->xp;
+  p.vp = c->vp;
+  p.jm = c->jm;
+  p.ctl = L->ctl;
+  p.st = c->status;
+  if (cudaMemsetAsync(L->ctl, 0, sizeof(ClusterCtl), c->stream) != cudaSuccess) return NB_ECUDA;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = sizeof(CSmem);
+  cfg.stream = c->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, cluster_loop_kernel, p) != cudaSuccess) {
+    cudaGetLastError();
+    return NB_ECUDA;
+  }
+  ClusterCtl h;
+  if (cudaMemcpyAsync(c->hpin, L->ctl, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return NB_ECUDA;
+  memcpy(&h, c->hpin, sizeof(h));
+  c->launches += 1;
+  c->steps += h.steps;
+  c->interactions += (double)h.interactions;
+  // the rows stayed in place and every corrected row's record was rewritten:
+  // the j-memory is current for the new state
+  c->state_ver++;
+  c->jm_ver = c->state_ver;
+  c->pred_valid = false;
+  c->f_valid = false;
+  return NB_OK;
+}

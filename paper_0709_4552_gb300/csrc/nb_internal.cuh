@@ -157,6 +157,7 @@ struct nb_ctx {
   double* h_ceps;
   void* ens;            // ensemble work area (ensemble.cu)
   void* loop;           // persistent-loop work area (persistent.cu)
+  void* cloop;          // cluster-loop work area (cluster.cu)
 };
 
 // ---- launchers (integrator.cu) -------------------------------------------
@@ -255,6 +256,11 @@ void nb_ensemble_free(nb_ctx* c);
 // (re)compute the spatial order within each cluster when it is due (mixed ensembles)
 int nb_ensemble_ensure_sorted(nb_ctx* c);
 int nb_integrate_graph(nb_ctx* c, double t_end);
+
+// cluster.cu: the block-step loop of one small mixed system on one thread-block cluster
+int nb_integrate_cluster(nb_ctx* c, double t_end);
+void nb_cluster_free(nb_ctx* c);
+int nb_cluster_size(nb_ctx* c);  // CTAs per cluster the GPU co-schedules (16, 8, or 0)
 
 // persistent.cu: the block-step loop of one system as one cooperative launch
 int nb_integrate_persistent(nb_ctx* c, double t_end);

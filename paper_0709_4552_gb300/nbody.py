@@ -26,8 +26,9 @@ NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ENUMERIC, NB_EDTMIN, NB_ETIMEOUT, NB_E
 NB_FP64, NB_MIXED = 0, 1
 NB_PTR_HOST, NB_PTR_DEVICE = 0, 1
 NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
-NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT = 0, 1, 2
+NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT, NB_LOOP_CLUSTER = 0, 1, 2, 3
 NB_PERSISTENT_MAX_N = 65536
+NB_CLUSTER_MAX_N = 16384
 NB_JPREDICT_AUTO = -1
 
 # every symbol include/nbody.h declares

@@ -138,7 +138,7 @@ def test_persistent_rejects_bad_arguments(nbl):
         assert e.value.code == nbl.NB_EINVAL
         s.clear_error()
         with pytest.raises(nbl.NBodyError) as e:
-            s.integrate(0.125, loop=3)
+            s.integrate(0.125, loop=4)
         assert e.value.code == nbl.NB_EINVAL
 
 
