@@ -2,8 +2,10 @@
 // thread-block cluster: the paper's ring algorithm (Sec. 4.3) on one chip.
 //
 // The C CTAs of a cluster (16 where the GPU can co-schedule them, else 8; one
-// per SM) each own a contiguous slice of at most 1024 rows -- their "N/p
-// particles" -- and keep it in shared memory, predicted to each block time on
+// per SM) each own at most 1024 rows -- their "N/p particles", dealt out in
+// blocks of 32 rows round-robin so that the active particles, which crowd in
+// a few regions of the spatial order, spread over every CTA's corrector --
+// and keep them in shared memory, predicted to each block time on
 // the fly from the j-memory (the GRAPE-style double-single records of
 // onboard.cu, Sec. 4.4 step 4).  Per block step (Sec. 4.1 steps 2-5):
 //   A  every CTA has published the minimum of t_i + dt_i over its rows and
@@ -44,6 +46,25 @@ constexpr int kGI = 256;       // active particles per force group
 constexpr int kChunk = 128;    // j per FP32 partial sum before the double-single fold
 constexpr int kMaxC = 16;      // CTAs per cluster at most
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;
+constexpr int kRB = 32;        // rows per ownership block (dealt round-robin to the CTAs)
+
+// row of own row index q of CTA me (blocks of kRB rows, block b owned by b % C)
+__device__ __forceinline__ int64_t own_row(int q, int me, int C) {
+  return ((int64_t)(q / kRB) * C + me) * kRB + (q % kRB);
+}
+// own row index of a row, or -1 when another CTA owns it
+__device__ __forceinline__ int own_index(int64_t row, int me, int C) {
+  const int64_t b = row / kRB;
+  return (int)(b % C) == me ? (int)((b / C) * kRB + row % kRB) : -1;
+}
+// rows CTA me owns
+__device__ __forceinline__ int own_count(int64_t N, int me, int C) {
+  const int64_t nb = (N + kRB - 1) / kRB;  // blocks
+  if (me >= nb) return 0;
+  const int64_t mine = (nb - 1 - me) / C + 1;  // blocks me, me + C, ...
+  const int64_t last = me + (mine - 1) * C;    // its last block (maybe partial)
+  return (int)((mine - 1) * kRB + min((int64_t)kRB, N - last * kRB));
+}
 
 struct ClusterCtl {
   long long steps;
@@ -71,6 +92,8 @@ struct CSmem {
   float ixh[kCRows], iyh[kCRows], izh[kCRows], ixl[kCRows], iyl[kCRows], izl[kCRows];
   float ivx[kCRows], ivy[kCRows], ivz[kCRows];
   int32_t irow[kCRows];
+  // own rows' next due time t_i + dt_i (bit pattern), kept by the corrector
+  unsigned long long due[kCRows];
   // the force group's i data, gathered from the owners
   float gxh[kGI], gyh[kGI], gzh[kGI], gxl[kGI], gyl[kGI], gzl[kGI], gvx[kGI], gvy[kGI], gvz[kGI];
   int32_t grow[kGI];
@@ -90,13 +113,10 @@ struct CSmem {
 };
 
 // minimum of t_i + dt_i over own rows and the rows at it -> s.pmin, s.pcnt
-__device__ void publish(const ClusterArgs& p, CSmem& s, int64_t r0, int nr) {
+__device__ void publish(const ClusterArgs& p, CSmem& s, int me, int C, int nr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   unsigned long long best = kInfBits;
-  for (int q = tid; q < nr; q += kCT) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]);
-    best = b < best ? b : best;
-  }
+  for (int q = tid; q < nr; q += kCT) best = s.due[q] < best ? s.due[q] : best;
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, best, o);
     best = u < best ? u : best;
@@ -106,8 +126,7 @@ __device__ void publish(const ClusterArgs& p, CSmem& s, int64_t r0, int nr) {
   best = kInfBits;
   for (int k = 0; k < kCT / 32; ++k) best = s.wmin[k] < best ? s.wmin[k] : best;
   int cnt = 0;
-  for (int q = tid; q < nr; q += kCT)
-    cnt += (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == best;
+  for (int q = tid; q < nr; q += kCT) cnt += s.due[q] == best;
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if (lane == 0) s.wcnt[w] = cnt;
   __syncthreads();
@@ -121,12 +140,12 @@ __device__ void publish(const ClusterArgs& p, CSmem& s, int64_t r0, int nr) {
 
 // own rows at the block time, ascending, into s.irow (each thread scans a
 // contiguous run of rows; a block scan places the runs in order)
-__device__ void list_rows(const ClusterArgs& p, CSmem& s, int64_t r0, int nr, unsigned long long tnb) {
+__device__ void list_rows(const ClusterArgs& p, CSmem& s, int me, int C, int nr, unsigned long long tnb) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int W = (nr + kCT - 1) / kCT;
   const int q0 = min(tid * W, nr), q1 = min(q0 + W, nr);
   int cnt = 0;
-  for (int q = q0; q < q1; ++q) cnt += (unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == tnb;
+  for (int q = q0; q < q1; ++q) cnt += s.due[q] == tnb;
   int inc = cnt;  // inclusive warp scan
   for (int o = 1; o < 32; o <<= 1) {
     const int u = __shfl_up_sync(0xffffffffu, inc, o);
@@ -138,7 +157,7 @@ __device__ void list_rows(const ClusterArgs& p, CSmem& s, int64_t r0, int nr, un
   for (int k = 0; k < w; ++k) base += s.wcnt[k];
   int at = base + inc - cnt;
   for (int q = q0; q < q1; ++q)
-    if ((unsigned long long)__double_as_longlong(p.t[r0 + q] + p.dt[r0 + q]) == tnb) s.irow[at++] = (int32_t)(r0 + q);
+    if (s.due[q] == tnb) s.irow[at++] = (int32_t)own_row(q, me, C);
   __syncthreads();
 }
 
@@ -155,12 +174,15 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int64_t N = p.N;
-  const int64_t R = (N + C - 1) / C;  // rows per CTA (<= kCRows, checked by the host)
-  const int64_t r0 = min((int64_t)me * R, N);
-  const int nr = (int)(min(r0 + R, N) - r0);
+  const int nr = own_count(N, me, C);  // <= kCRows (checked by the host)
   long long steps = 0;
 
-  publish(p, s, r0, nr);
+  for (int q = tid; q < nr; q += kCT) {
+    const int64_t r = own_row(q, me, C);
+    s.due[q] = (unsigned long long)__double_as_longlong(p.t[r] + p.dt[r]);
+  }
+  __syncthreads();
+  publish(p, s, me, C, nr);
   for (;;) {
     cl.sync();  // A: every CTA's minimum and count are published
     if (tid < 32) {  // lane c reads CTA c's pair; the minimum and the offsets by shuffles
@@ -200,7 +222,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
     }
     const int mine = s.cmine[me], before = s.cbefore[me];
     const unsigned long long tnb = (unsigned long long)__double_as_longlong(tn);
-    list_rows(p, s, r0, nr, tnb);
+    list_rows(p, s, me, C, nr, tnb);
     // own active particles: FP64 prediction (step 3) kept for the corrector,
     // double-single i data for the forces
     for (int k = tid; k < mine; k += kCT) {
@@ -221,7 +243,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
     }
     // own j rows predicted on the fly from the j-memory (Sec. 4.4 step 4)
     for (int q = tid; q < nr; q += kCT) {
-      const int64_t row = r0 + q;
+      const int64_t row = own_row(q, me, C);
       const float4 R0 = p.jm[row], R1 = p.jm[p.n_pad + row], R2 = p.jm[2 * p.n_pad + row],
                    R3 = p.jm[3 * p.n_pad + row], R4 = p.jm[4 * p.n_pad + row];
       const float h = __double2float_rn(tn - p.t[row]);
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
         if (i < gn) {
           const float xh = s.gxh[i], yh = s.gyh[i], zh = s.gzh[i], xl = s.gxl[i], yl = s.gyl[i], zl = s.gzl[i];
           const float vx = s.gvx[i], vy = s.gvy[i], vz = s.gvz[i];
-          const int64_t self = (int64_t)s.grow[i] - r0;
+          const int self = own_index(s.grow[i], me, C);  // -1: held by another CTA
           const int q0 = (int)((int64_t)part * nr / P), q1 = (int)((int64_t)(part + 1) * nr / P);
           for (int c0 = q0; c0 < q1; c0 += kChunk) {
             const int c1 = min(c0 + kChunk, q1);
@@ -342,10 +364,13 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) fo[c] = have ? s.fsum[c][pos - (int)g0] : 0.0;
         const int64_t row = have ? (int64_t)s.irow[pos - before] : (int64_t)s.irow[lo_pos - before];
-        nbh::correct_row_lanes4(row, p.n_pad, tn, fo, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t,
-                                p.dt, p.xp, p.vp, p.st, sub, (tid & 31) - sub, have);
+        const double nd = nbh::correct_row_lanes4(row, p.n_pad, tn, fo, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk,
+                                                  p.pot, p.t, p.dt, p.xp, p.vp, p.st, sub, (tid & 31) - sub, have);
         __syncwarp();
-        if (have && sub == 0) nbh::write_jm_record(row, N, p.n_pad, p.m, p.x, p.v, p.a, p.jk, p.dt, p.jm);
+        if (have && sub == 0) {
+          nbh::write_jm_record(row, N, p.n_pad, p.m, p.x, p.v, p.a, p.jk, p.dt, p.jm);
+          s.due[own_index(row, me, C)] = (unsigned long long)__double_as_longlong(nd);
+        }
       }
       __syncthreads();
       if (g0 + kGI < n) cl.sync();  // D: the partials are read before the next group's are written
@@ -356,7 +381,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       p.ctl->interactions += n * (long long)N;
     }
     __syncthreads();
-    publish(p, s, r0, nr);
+    publish(p, s, me, C, nr);
   }
 }
 
@@ -416,7 +441,7 @@ int nb_integrate_cluster(nb_ctx* c, double t_end) {
   if (c->precision != NB_MIXED || c->n_clusters > 0) return NB_EINVAL;
   const int C = nb_cluster_size(c);
   if (C < 1) return NB_ECUDA;
-  if (c->n > (int64_t)C * kCRows) return NB_EINVAL;
+  if (c->n > (int64_t)C * kCRows) return NB_EINVAL;  // (whole blocks of kRB rows per CTA: kCRows / kRB of them)
   CLoop* L = static_cast<CLoop*>(c->cloop);
   if (!L->ctl && cudaMalloc((void**)&L->ctl, sizeof(ClusterCtl)) != cudaSuccess) {
     cudaGetLastError();

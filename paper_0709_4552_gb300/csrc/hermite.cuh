@@ -156,8 +156,9 @@ __device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, 
 // shuffles use the full mask and are taken unconditionally.  `base` is the
 // warp lane of the group's lane 0; `write` says whether this group's row is
 // real (lanes of groups without a row, and lanes sub >= 4, compute on a
-// valid row and write nothing).
-__device__ __forceinline__ void correct_row_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
+// valid row and write nothing).  Returns, on the group's lane 0 of a real
+// row, the row's next due time t + dt_new (0 elsewhere).
+__device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
                                                    double eta, double dt_min, double dt_max, double* __restrict__ x,
                                                    double* __restrict__ v, double* __restrict__ a,
                                                    double* __restrict__ jk, double* __restrict__ pot,
@@ -215,7 +216,7 @@ __device__ __forceinline__ void correct_row_lanes4(int64_t i, int64_t n_pad, dou
   const double nj = __shfl_sync(0xffffffffu, root, base + 1);
   const double n2 = __shfl_sync(0xffffffffu, root, base + 2);
   const double n3 = __shfl_sync(0xffffffffu, root, base + 3);
-  if (!write || sub != 0) return;
+  if (!write || sub != 0) return 0.0;
   const double p1 = f[6];
   pot[i] = p1;
   const double num = na * n2 + nj * nj;
@@ -236,6 +237,7 @@ __device__ __forceinline__ void correct_row_lanes4(int64_t i, int64_t n_pad, dou
   if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
   ti[i] = t;
   dt[i] = dnew;
+  return t + dnew;
 }
 
 // j-memory record of row i (the on-the-fly j prediction's input, Sec. 4.4
