@@ -507,7 +507,10 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
 #pragma unroll
     for (int c = 0; c < 7; ++c) NB_ACC_ZERO(k, c);
   }
-  // box of the warp's i-particles (hi parts) and their largest |coordinate|
+  // box of this thread's i-particles (hi parts) and their largest
+  // |coordinate|: the far test is taken per thread and the tile is far for
+  // the warp when it is far for every lane (a warp of scattered particles,
+  // as a small random block forms, still finds the tiles far from all of them)
   float wlo[3], whi[3], wr = 0.0f;
   if (tbox) {
 #pragma unroll
@@ -520,14 +523,6 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
         whi[c] = fmaxf(whi[c], xh[k][c]);
       }
       wr = fmaxf(wr, fmaxf(fabsf(wlo[c]), fabsf(whi[c])));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        wlo[c] = fminf(wlo[c], __shfl_xor_sync(0xffffffffu, wlo[c], o));
-        whi[c] = fmaxf(whi[c], __shfl_xor_sync(0xffffffffu, whi[c], o));
-      }
-      wr = fmaxf(wr, __shfl_xor_sync(0xffffffffu, wr, o));
     }
   }
 
@@ -604,8 +599,9 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
 #pragma unroll
       for (int c = 0; c < 7; ++c) p[k][c] = 0.0f;
 
-    // far test (warp-uniform): box gap >= theta (|x|max of warp + |x|max of
-    // tile) bounds the hi-only difference error by 2^-24 (1/theta + 1).
+    // far test: box gap >= theta (|x|max of the thread's i + |x|max of the
+    // tile) bounds the hi-only difference error of each of its pairs by
+    // 2^-24 (1/theta + 1); the warp takes the far pass when every lane passes.
     // Boxes cover NB_BOX_TILE slots: a longer tile needs all of its boxes
     // far, a shorter one uses the box that contains it.
     bool far = false;
