@@ -88,7 +88,8 @@ __device__ __forceinline__ void store_predicted(int64_t i, int64_t n_pad, const 
 // New step: Aarseth criterion at the end of the step (a2e = a2 + a3 h),
 // largest power of two below it within [dt_min, dt_max]; it may shrink
 // freely and doubles only when t is a multiple of the doubled step.
-__device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, const double (&f)[7], double eta,
+// Returns the row's next due time t + dt_new.
+__device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t, const double (&f)[7], double eta,
                                             double dt_min, double dt_max, double* __restrict__ x,
                                             double* __restrict__ v, double* __restrict__ a,
                                             double* __restrict__ jk, double* __restrict__ pot,
@@ -142,6 +143,7 @@ __device__ __forceinline__ void correct_row(int64_t i, int64_t n_pad, double t, 
   if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
   ti[i] = t;
   dt[i] = dnew;
+  return t + dnew;
 }
 
 // The same correction spread over four lanes of a warp: lane `sub` < 3 of

@@ -112,12 +112,15 @@ __device__ bool grid_barrier(LoopCtl* ctl, unsigned long long& epoch, unsigned i
     int ok = 1;
     const long long t0 = globaltimer_ns();
     unsigned int polls = 0;
+    // the counter alone in the common path; the abort flag and the clock
+    // every 16th poll (one L2 round trip per poll instead of two)
     while (ld_acquire_u64(&ctl->bar) < target) {
+      if ((++polls & 15u) != 0u) continue;
       if (*(volatile unsigned int*)&ctl->abort) {
         ok = 0;
         break;
       }
-      if (++polls >= kPollCap || globaltimer_ns() - t0 > wait_ns) {
+      if (polls >= kPollCap || globaltimer_ns() - t0 > wait_ns) {
         atomicOr(&ctl->abort, 1u);
         atomicOr(&st->flags, NB_ST_TIMEOUT);
         ok = 0;
@@ -141,7 +144,12 @@ __device__ __forceinline__ void min_count(unsigned long long& v, int& c, unsigne
   }
 }
 
+constexpr int kLDue = 512;  // own rows whose due times a CTA keeps in shared memory
+
 struct LoopSmem {
+  // own rows' next due time t_i + dt_i (bit pattern), kept by the corrector
+  // when the CTA owns at most kLDue rows (else read from the state)
+  unsigned long long due[kLDue];
   int rank;                // this CTA's rank among the CTAs on its SM
   long long item;
   unsigned long long wv[kLWarps];
@@ -155,14 +163,20 @@ struct LoopSmem {
   int ok;
 };
 
+// due time of own row i (bit pattern)
+__device__ __forceinline__ unsigned long long due_of(const LoopArgs& p, const LoopSmem& s, int64_t i, int64_t r0,
+                                                     bool cached) {
+  return cached ? s.due[i - r0] : (unsigned long long)__double_as_longlong(p.t[i] + p.dt[i]);
+}
+
 // minimum of t_i + dt_i over rows [r0, r1) and the number of rows at it,
 // published for the other CTAs (positive doubles order like their bits)
 __device__ void publish_slice(const LoopArgs& p, int64_t r0, int64_t r1, LoopSmem& s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool cached = r1 - r0 <= kLDue;
   unsigned long long best = kInfBits;
   int cnt = 0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kLT)
-    min_count(best, cnt, (unsigned long long)__double_as_longlong(p.t[i] + p.dt[i]), 1);
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kLT) min_count(best, cnt, due_of(p, s, i, r0, cached), 1);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -246,9 +260,10 @@ __device__ void read_slices(const LoopArgs& p, unsigned int G, LoopSmem& s) {
 __device__ void write_active(const LoopArgs& p, int64_t r0, int64_t r1, unsigned long long tnb, long long base,
                              LoopSmem& s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool cached = r1 - r0 <= kLDue;
   for (int64_t r = r0; r < r1; r += kLT) {
     const int64_t i = r + threadIdx.x;
-    const bool on = i < r1 && (unsigned long long)__double_as_longlong(p.t[i] + p.dt[i]) == tnb;
+    const bool on = i < r1 && due_of(p, s, i, r0, cached) == tnb;
     const unsigned int ball = __ballot_sync(0xffffffffu, on);
     if (lane == 0) s.wc[warp] = __popc(ball);
     __syncthreads();
@@ -335,7 +350,7 @@ __device__ __forceinline__ int64_t loop_splits(int64_t n, int64_t jtiles, unsign
 // of this CTA's own list positions [before, before + mycnt).  The step's
 // values are read from shared memory here rather than kept in registers
 // across the force items.
-__device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles, unsigned int G, int64_t r0,
+__device__ void correct_own(const LoopArgs& p, LoopSmem& s, int64_t jtiles, unsigned int G, int64_t r0,
                             int64_t r1) {
   const long long before = s.before;
   const int mycnt = s.mycnt;
@@ -377,6 +392,7 @@ __device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles
         for (int r = 0; r < 7; ++r) f[r] += __shfl_xor_sync(0xffffffffu, f[r], o);
       f[6] = -f[6];
     }
+    const bool cached = r1 - r0 <= kLDue;
     if (L >= 4) {
       // every lane of the CTA takes this branch (L is uniform) and every
       // shuffle inside; lanes without a row read a valid own row, write nothing
@@ -385,13 +401,15 @@ __device__ void correct_own(const LoopArgs& p, const LoopSmem& s, int64_t jtiles
       if (!(have && l < 4))
 #pragma unroll
         for (int r = 0; r < 7; ++r) f[r] = 0.0;
-      nbh::correct_row_lanes4(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t, p.dt,
-                              p.xp, p.vp, p.st, l, (int)(threadIdx.x & 31) - l, have);
+      const double nd = nbh::correct_row_lanes4(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk,
+                                                p.pot, p.t, p.dt, p.xp, p.vp, p.st, l, (int)(threadIdx.x & 31) - l, have);
+      if (have && l == 0 && cached) s.due[i - r0] = (unsigned long long)__double_as_longlong(nd);
     } else if (have && l == 0) {
       int64_t i = p.act[k];
       i = i < r0 ? r0 : (i >= r1 ? r1 - 1 : i);  // own rows only
-      nbh::correct_row(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot, p.t, p.dt, p.xp,
-                       p.vp, p.st);
+      const double nd = nbh::correct_row(i, p.n_pad, tn, f, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk, p.pot,
+                                         p.t, p.dt, p.xp, p.vp, p.st);
+      if (cached) s.due[i - r0] = (unsigned long long)__double_as_longlong(nd);
     }
   }
 }
@@ -429,6 +447,10 @@ __global__ void __launch_bounds__(kLT, kLMaxPerSm) loop_kernel(LoopArgs p) {
       const double px[3] = {NB_PAD_POS, NB_PAD_POS, NB_PAD_POS}, pv[3] = {0.0, 0.0, 0.0};
       nbh::store_predicted(i, p.n_pad, px, pv, 0.0, p.xp, p.vp, p.jA, p.jB, p.jC, true, MIXED);
     }
+  if (r1 - r0 <= kLDue)
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += kLT)
+      s.due[i - r0] = (unsigned long long)__double_as_longlong(p.t[i] + p.dt[i]);
+  __syncthreads();
   publish_slice(p, r0, r1, s);
 
   for (;;) {
