@@ -68,6 +68,8 @@ def parse():
                          "N-body time unit vs N and the per-task model; one JSON line each")
     ap.add_argument("--tune-file", default="",
                     help="c3sweep / c4: save the autotuned table to this JSON file (c3sweep adds to it)")
+    ap.add_argument("--sweep-n", default="",
+                    help="c3sweep: active-block sizes to run (comma list; default the whole sweep)")
     ap.add_argument("--tapp-sizes", default="1024,2048,4096,8192,16384,32768,65536,131072,196608")
     return ap.parse_args()
 
@@ -445,7 +447,10 @@ def run_integration(args):
         state = (m, x, v, st["a"], st["jerk"], ti, st["dt"])
         xp, vp = oracle.predict(x, v, st["a"], st["jerk"], ti, T)
         res = []
-        for n in (256, 1024, 2048, 4096, 8192, inputs.block_size(N), 65536, N):
+        sweep = (256, 1024, 2048, 4096, 8192, inputs.block_size(N), 65536, N)
+        if args.sweep_n:
+            sweep = tuple(int(k) for k in args.sweep_n.split(","))
+        for n in sweep:
             act = inputs.sample_indices(N, n, 1003).astype(np.int32)
             pos = inputs.sample_indices(n, min(n, 1024), 2003)
             ref = oracle.forces(m, xp, vp, eps, idx=act[pos].astype(np.int64), compensated=True)

@@ -25,7 +25,13 @@ context driven through the C ABI; all arithmetic of a step runs in its CUDA
 kernels.  This module only moves data between ranks and orders the calls.
 Blocks travel as tensors on the communicator's device: CUDA tensors with
 NCCL (the engine then reads and writes device pointers), host tensors with
-gloo.  No TMA multicast or NVLink multicast is used anywhere.
+gloo.  No TMA multicast or NVLink multicast is used anywhere.  On device
+pointers the engine's calls are asynchronous on the engine's stream while
+torch's tensor operations and NCCL's collectives are ordered on torch's
+current stream; an engine created on that stream
+(``NBody(..., stream=torch.cuda.current_stream())``) needs nothing more,
+any other engine is fenced with a device synchronisation wherever a tensor
+passes between the two (:func:`_fence`).
 
 Determinism: on the FP64 path the copy algorithm sums every force over all N
 in the same j order as one rank, so with one j-split per force call (the
@@ -114,6 +120,19 @@ class Comm:
         return got
 
 
+def _fence(engine, comm):
+    """Orders the engine's kernels against torch's work on CUDA tensors at a
+    hand-off: nothing when the engine works on torch's current stream (or the
+    tensors live on the host, where the engine's calls synchronise), else a
+    synchronisation of the device (both directions at once)."""
+    if comm.device.type != "cuda":
+        return
+    h = getattr(engine, "stream_handle", None)
+    if h is not None and h == comm.torch.cuda.current_stream(comm.device).cuda_stream:
+        return
+    comm.torch.cuda.synchronize(comm.device)
+
+
 def _index(comm, idx):
     return comm.tensor(np.ascontiguousarray(idx, dtype=np.int32), comm.torch.int32)
 
@@ -127,16 +146,17 @@ def copy_step(engine, comm, lo, hi):
     mine = idx[(idx >= lo) & (idx < hi)]
     k = len(mine)
     dmine = _index(comm, mine)
-    if k:
-        f = [torch.empty((k, 3), dtype=torch.float64, device=comm.device) for _ in range(2)]
-        f.append(torch.empty(k, dtype=torch.float64, device=comm.device))
-        engine.compute_forces(dmine, *f)
-        engine.correct(dmine, t)
+    f = [torch.empty((k, 3), dtype=torch.float64, device=comm.device) for _ in range(2)]
+    f.append(torch.empty(k, dtype=torch.float64, device=comm.device))
     # the corrected block of this rank: index + x v a jerk pot t dt (18 columns)
     out = {key: torch.empty((k,) if _WIDTH[key] == 1 else (k, 3), dtype=torch.float64, device=comm.device)
            for key in _KEYS}
+    _fence(engine, comm)
     if k:
+        engine.compute_forces(dmine, *f)
+        engine.correct(dmine, t)
         engine.get_particles_idx(dmine, out=out)
+    _fence(engine, comm)
     rows = torch.cat([dmine.to(torch.float64)[:, None]] + [out[key].reshape(k, _WIDTH[key]) for key in _KEYS],
                      dim=1)
     blocks = comm.allgatherv(rows)
@@ -150,7 +170,9 @@ def copy_step(engine, comm, lo, hi):
             vals[key] = rows[:, c0:c0 + w].reshape(-1) if w == 1 else rows[:, c0:c0 + w].contiguous()
             vals[key] = vals[key].contiguous()
             c0 += w
+        _fence(engine, comm)
         engine.set_particles_idx(oidx, vals)
+        _fence(engine, comm)
     return t, n
 
 
@@ -171,7 +193,9 @@ def ring_step(engine, comm, base):
     if k:
         xp = torch.empty((k, 3), dtype=torch.float64, device=comm.device)
         vp = torch.empty_like(xp)
+        _fence(engine, comm)
         engine.get_predicted(dmine, xp, vp)
+        _fence(engine, comm)
         block[:, 0:3] = xp
         block[:, 3:6] = vp
         block[:, 6] = dmine.to(torch.float64) + base
@@ -182,13 +206,17 @@ def ring_step(engine, comm, base):
             gid = block[:, 6].to(torch.int64).contiguous()
             acc, jerk = block[:, 7:10].contiguous(), block[:, 10:13].contiguous()
             pot = block[:, 13].contiguous()
+            _fence(engine, comm)
             engine.forces_on(xi, vi, gid, base, acc, jerk, pot, accumulate=True)
+            _fence(engine, comm)
             block[:, 7:10], block[:, 10:13], block[:, 13] = acc, jerk, pot
         block = comm.shift(block)
     if k:
-        engine.set_forces(dmine, block[:, 7:10].contiguous(), block[:, 10:13].contiguous(),
-                          block[:, 13].contiguous())
+        fa, fj, fp = block[:, 7:10].contiguous(), block[:, 10:13].contiguous(), block[:, 13].contiguous()
+        _fence(engine, comm)
+        engine.set_forces(dmine, fa, fj, fp)
         engine.correct(dmine, t)
+        _fence(engine, comm)
     return t, n_all
 
 
@@ -204,7 +232,9 @@ def ring_initialize(engine, comm, base):
     own = _index(comm, np.arange(N_r, dtype=np.int32))
     xp = torch.empty((N_r, 3), dtype=torch.float64, device=comm.device)
     vp = torch.empty_like(xp)
+    _fence(engine, comm)
     engine.get_predicted(own, xp, vp)
+    _fence(engine, comm)
     block = torch.zeros((N_r, 14), dtype=torch.float64, device=comm.device)
     block[:, 0:3], block[:, 3:6] = xp, vp
     block[:, 6] = own.to(torch.float64) + base
@@ -212,11 +242,16 @@ def ring_initialize(engine, comm, base):
         if block.shape[0]:
             acc, jerk = block[:, 7:10].contiguous(), block[:, 10:13].contiguous()
             pot = block[:, 13].contiguous()
-            engine.forces_on(block[:, 0:3].contiguous(), block[:, 3:6].contiguous(),
-                             block[:, 6].to(torch.int64).contiguous(), base, acc, jerk, pot, accumulate=True)
+            xi, vi, gid = block[:, 0:3].contiguous(), block[:, 3:6].contiguous(), block[:, 6].to(torch.int64).contiguous()
+            _fence(engine, comm)
+            engine.forces_on(xi, vi, gid, base, acc, jerk, pot, accumulate=True)
+            _fence(engine, comm)
             block[:, 7:10], block[:, 10:13], block[:, 13] = acc, jerk, pot
         block = comm.shift(block)
-    engine.set_initial_forces(block[:, 7:10].contiguous(), block[:, 10:13].contiguous(), block[:, 13].contiguous())
+    fa, fj, fp = block[:, 7:10].contiguous(), block[:, 10:13].contiguous(), block[:, 13].contiguous()
+    _fence(engine, comm)
+    engine.set_initial_forces(fa, fj, fp)
+    _fence(engine, comm)
 
 
 def integrate(engine, comm, t_end, algorithm, N=None, base=0, max_steps=None):

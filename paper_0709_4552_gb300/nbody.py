@@ -586,6 +586,9 @@ class NBody:
 
     def __init__(self, n_max, precision=NB_MIXED, device=0, stream=None):
         self.ctx = nb_create(n_max, precision, device, stream)
+        # the cudaStream_t handle the context works on as torch reports it
+        # (0 = torch's default stream), None for a stream of the library's own
+        self.stream_handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
 
     def close(self):
         if self.ctx is not None:

@@ -4,7 +4,9 @@ exchanging host buffers over gloo (the kernels of the two ranks never wait on
 each other; the host collectives do the waiting).  FP64: the copy algorithm
 repeats a one-rank run with one j-split bit for bit, and the two-rank ring a
 one-rank run with two j-splits at the same boundary; mixed: both follow the
-one-rank run within the mixed path's reach and the oracle pins the forces."""
+one-rank run within the mixed path's reach and the oracle pins the forces.
+One rank on NCCL runs the device data path (CUDA tensors, device pointers)
+and repeats the one-rank run bit for bit."""
 import os
 import socket
 import sys
@@ -138,3 +140,50 @@ def test_mixed_follows_one_rank_and_oracle(nbl, algorithm):
     # energy drift within 2x the oracle's own over the same integration
     orc = _oracle_run(N, t_end)
     assert _energy_drift(N, got) <= 2 * _energy_drift(N, orc) + 1e-9
+
+
+def _nccl_main(rank, port, algorithm, same_stream, out):
+    # one rank on NCCL: the blocks travel as CUDA tensors and the context reads
+    # and writes device pointers (the multi-GPU data path, at p = 1), on
+    # torch's current stream or on a stream of its own (fenced)
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_0709_4552_gb300 import distributed as D, nbody as nb
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    comm = D.Comm("cuda:0")
+    N, t_end = 1024, 2.0 ** -5
+    m, x, v = inputs.plummer(N, 77, "salpeter")
+    s = nb.NBody(N, nb.NB_FP64, 0, stream=torch.cuda.current_stream() if same_stream else None)
+    s.set_params(EPS, ETA, 2.0 ** -22, t_end)
+    s.set_tuning(n_split=1)
+    s.set_j_particles(0, m, x, v)
+    if algorithm == "copy":
+        s.initial_forces_and_dt()
+        steps = D.integrate(s, comm, t_end, "copy", N=N)
+    else:
+        D.ring_initialize(s, comm, 0)
+        steps = D.integrate(s, comm, t_end, "ring", base=0)
+    torch.cuda.synchronize()
+    st = s.get_particles(0, N)
+    s.close()
+    out[0] = dict(steps=steps, **{k: st[k] for k in ("x", "v", "a", "t", "dt")})
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("algorithm,same_stream", [("copy", False), ("ring", False), ("ring", True)])
+def test_nccl_device_path_single_rank(nbl, algorithm, same_stream):
+    torch = pytest.importorskip("torch")
+    if not torch.distributed.is_nccl_available():
+        pytest.skip("no NCCL")
+    N, t_end = 1024, 2.0 ** -5
+    ref, steps = _one_rank(nbl, nbl.NB_FP64, N, t_end, 1)
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_nccl_main, args=(_free_port(), algorithm, same_stream, out), nprocs=1, join=True, start_method="spawn")
+    got = out[0]
+    assert got["steps"] == steps
+    for k in ("x", "v", "a", "t", "dt"):
+        assert np.array_equal(got[k], ref[k]), k
