@@ -45,6 +45,7 @@ constexpr int kCRows = 1024;   // rows per CTA at most
 constexpr int kGI = 256;       // active particles per force group
 constexpr int kChunk = 128;    // j per FP32 partial sum before the double-single fold
 constexpr int kMaxC = 16;      // CTAs per cluster at most
+constexpr int kCC = 256;       // own active particles whose corrector inputs stay in shared memory
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;
 constexpr int kRB = 32;        // rows per ownership block (dealt round-robin to the CTAs)
 
@@ -66,6 +67,16 @@ __device__ __forceinline__ int own_count(int64_t N, int me, int C) {
   return (int)((mine - 1) * kRB + min((int64_t)kRB, N - last * kRB));
 }
 
+// (hi, lo) += (bh, bl): double-single sum (Knuth's TwoSum of the high parts,
+// the low parts and the rounding error added without renormalisation, as the
+// force item's fold)
+__device__ __forceinline__ void ds_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  lo = (lo + bl) + ((hi - (s - bb)) + (bh - bb));
+  hi = s;
+}
+
 struct ClusterCtl {
   long long steps;
   long long interactions;
@@ -85,25 +96,29 @@ struct ClusterArgs {
 };
 
 struct CSmem {
+  // own active particles in list order, predicted (double-single positions,
+  // FP32 velocities): A = (xh, yh, zh, vx), B = (xl, yl, zl, vy), C = (vz, row bits)
+  float4 iA[kCRows], iB[kCRows];
+  float2 iC[kCRows];
+  // the force group's i data, the same layout (group 0 pushed by the owners,
+  // later groups gathered from them)
+  float4 gA[kGI], gB[kGI];
+  float2 gC[kGI];
+  // every CTA's (minimum of t_i + dt_i over its rows, rows at it), pushed by each
+  ulonglong2 pairs[kMaxC];
   // own rows predicted to the block time (double-single positions, FP32 v, m)
   float jxh[kCRows], jyh[kCRows], jzh[kCRows], jxl[kCRows], jyl[kCRows], jzl[kCRows];
   float jvx[kCRows], jvy[kCRows], jvz[kCRows], jms[kCRows];
-  // own active particles in list order: predicted i data and their rows
-  float ixh[kCRows], iyh[kCRows], izh[kCRows], ixl[kCRows], iyl[kCRows], izl[kCRows];
-  float ivx[kCRows], ivy[kCRows], ivz[kCRows];
   int32_t irow[kCRows];
   // own rows' next due time t_i + dt_i (bit pattern), kept by the corrector
   unsigned long long due[kCRows];
-  // the force group's i data, gathered from the owners
-  float gxh[kGI], gyh[kGI], gzh[kGI], gxl[kGI], gyl[kGI], gzl[kGI], gvx[kGI], gvy[kGI], gvz[kGI];
-  int32_t grow[kGI];
-  // this CTA's partial sums on the group (read by the owners)
-  double part[7][kGI];
+  // this CTA's double-single partial sums on the group (read by the owners)
+  float2 part[7][kGI];
   // the owner's sums of its particles of the group (all CTAs' partials)
   double fsum[7][kGI];
-  // published: minimum of t_i + dt_i over own rows (bit pattern), rows at it
-  unsigned long long pmin;
-  int pcnt;
+  // corrector inputs of own active particles k < kCC, kept from their
+  // prediction: old t, dt, acceleration, jerk and the predicted x, v
+  double cT[kCC], cDT[kCC], cA0[3][kCC], cJ0[3][kCC], cXP[3][kCC], cVP[3][kCC];
   // every CTA's offset and count in the active list (read at barrier A)
   int cbefore[kMaxC], cmine[kMaxC];
   double tn;
@@ -112,8 +127,9 @@ struct CSmem {
   int wcnt[kCT / 32];
 };
 
-// minimum of t_i + dt_i over own rows and the rows at it -> s.pmin, s.pcnt
-__device__ void publish(const ClusterArgs& p, CSmem& s, int me, int C, int nr) {
+// minimum of t_i + dt_i over own rows and the rows at it, pushed into every
+// CTA's pairs[me] (read there after the next cluster barrier)
+__device__ void publish(CSmem& s, cg::cluster_group& cl, int me, int C, int nr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   unsigned long long best = kInfBits;
   for (int q = tid; q < nr; q += kCT) best = s.due[q] < best ? s.due[q] : best;
@@ -130,17 +146,16 @@ __device__ void publish(const ClusterArgs& p, CSmem& s, int me, int C, int nr) {
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if (lane == 0) s.wcnt[w] = cnt;
   __syncthreads();
-  if (tid == 0) {
+  if (tid < C) {
     int c = 0;
     for (int k = 0; k < kCT / 32; ++k) c += s.wcnt[k];
-    s.pmin = best;
-    s.pcnt = c;
+    *cl.map_shared_rank(&s.pairs[me], tid) = make_ulonglong2(best, (unsigned long long)c);
   }
 }
 
 // own rows at the block time, ascending, into s.irow (each thread scans a
 // contiguous run of rows; a block scan places the runs in order)
-__device__ void list_rows(const ClusterArgs& p, CSmem& s, int me, int C, int nr, unsigned long long tnb) {
+__device__ void list_rows(CSmem& s, int me, int C, int nr, unsigned long long tnb) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int W = (nr + kCT - 1) / kCT;
   const int q0 = min(tid * W, nr), q1 = min(q0 + W, nr);
@@ -182,12 +197,14 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
     s.due[q] = (unsigned long long)__double_as_longlong(p.t[r] + p.dt[r]);
   }
   __syncthreads();
-  publish(p, s, me, C, nr);
+  cl.sync();  // every CTA of the cluster runs before any writes another's shared memory
+  publish(s, cl, me, C, nr);
   for (;;) {
-    cl.sync();  // A: every CTA's minimum and count are published
-    if (tid < 32) {  // lane c reads CTA c's pair; the minimum and the offsets by shuffles
-      const unsigned long long pm = tid < C ? *cl.map_shared_rank(&s.pmin, tid) : kInfBits;
-      const int pc = tid < C ? *cl.map_shared_rank(&s.pcnt, tid) : 0;
+    cl.sync();  // A: every CTA's minimum and count are in every CTA's pairs
+    if (tid < 32) {  // lane c holds CTA c's pair; the minimum and the offsets by shuffles
+      const ulonglong2 pr = tid < C ? s.pairs[tid] : make_ulonglong2(kInfBits, 0ULL);
+      const unsigned long long pm = pr.x;
+      const int pc = (int)pr.y;
       unsigned long long tb = pm;
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long u = __shfl_xor_sync(0xffffffffu, tb, o);
@@ -222,27 +239,49 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
     }
     const int mine = s.cmine[me], before = s.cbefore[me];
     const unsigned long long tnb = (unsigned long long)__double_as_longlong(tn);
-    list_rows(p, s, me, C, nr, tnb);
-    // own active particles: FP64 prediction (step 3) kept for the corrector,
-    // double-single i data for the forces
+    list_rows(s, me, C, nr, tnb);
+    // the first iw threads (whole warps) predict the own active particles,
+    // the others the own j rows: the two global round trips overlap
+    const int iw = min(kCT, (mine + 31) & ~31);
+    // own active particles: FP64 prediction (step 3), double-single i data
+    // for the forces, and the corrector's inputs
     for (int k = tid; k < mine; k += kCT) {
       const int64_t row = s.irow[k];
-      double px[3], pv[3];
-      nbh::taylor(row, p.n_pad, tn - p.t[row], p.x, p.v, p.a, p.jk, px, pv);
+      const double t0 = p.t[row], dt0 = p.dt[row];
+      double a0[3], j0[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        p.xp[d * p.n_pad + row] = px[d];
-        p.vp[d * p.n_pad + row] = pv[d];
+        a0[d] = p.a[d * p.n_pad + row];
+        j0[d] = p.jk[d * p.n_pad + row];
       }
-      split_ds(px[0], s.ixh[k], s.ixl[k]);
-      split_ds(px[1], s.iyh[k], s.iyl[k]);
-      split_ds(px[2], s.izh[k], s.izl[k]);
-      s.ivx[k] = __double2float_rn(pv[0]);
-      s.ivy[k] = __double2float_rn(pv[1]);
-      s.ivz[k] = __double2float_rn(pv[2]);
+      double px[3], pv[3];
+      nbh::taylor(row, p.n_pad, tn - t0, p.x, p.v, p.a, p.jk, px, pv);
+      if (k < kCC) {
+        s.cT[k] = t0;
+        s.cDT[k] = dt0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          s.cA0[d][k] = a0[d];
+          s.cJ0[d][k] = j0[d];
+          s.cXP[d][k] = px[d];
+          s.cVP[d][k] = pv[d];
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          p.xp[d * p.n_pad + row] = px[d];
+          p.vp[d * p.n_pad + row] = pv[d];
+        }
+      }
+      float xh[3], xl[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) split_ds(px[d], xh[d], xl[d]);
+      s.iA[k] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(pv[0]));
+      s.iB[k] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(pv[1]));
+      s.iC[k] = make_float2(__double2float_rn(pv[2]), __int_as_float((int)row));
     }
     // own j rows predicted on the fly from the j-memory (Sec. 4.4 step 4)
-    for (int q = tid; q < nr; q += kCT) {
+    for (int q = (tid - iw + kCT) % kCT; q < nr; q += kCT) {
       const int64_t row = own_row(q, me, C);
       const float4 R0 = p.jm[row], R1 = p.jm[p.n_pad + row], R2 = p.jm[2 * p.n_pad + row],
                    R3 = p.jm[3 * p.n_pad + row], R4 = p.jm[4 * p.n_pad + row];
@@ -258,89 +297,96 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       s.jms[q] = R0.w;
     }
     __syncthreads();
-    cl.sync();  // B: every CTA's i data is ready
+    // push this CTA's particles of the first group into every CTA's group
+    // buffer (every CTA finished reading its buffer before barrier A)
+    {
+      const int npush = max(0, min(mine, kGI - before));
+      for (int e = tid; e < npush * C; e += kCT) {
+        const int k = e / C, c = e - (e / C) * C;
+        *cl.map_shared_rank(&s.gA[before + k], c) = s.iA[k];
+        *cl.map_shared_rank(&s.gB[before + k], c) = s.iB[k];
+        *cl.map_shared_rank(&s.gC[before + k], c) = s.iC[k];
+      }
+    }
+    cl.sync();  // B: the first group's i data is in every CTA, every CTA's i data is ready
 
     for (long long g0 = 0; g0 < n; g0 += kGI) {
       const int gn = (int)min((long long)kGI, n - g0);
-      // the group's i data from its owners' shared memory
-      for (int k = tid; k < gn; k += kCT) {
-        const int pos = (int)(g0 + k);
-        int c = 0;
-        while (c + 1 < C && s.cbefore[c + 1] <= pos) ++c;
-        const int a = pos - s.cbefore[c];
-        s.gxh[k] = *cl.map_shared_rank(&s.ixh[a], c);
-        s.gyh[k] = *cl.map_shared_rank(&s.iyh[a], c);
-        s.gzh[k] = *cl.map_shared_rank(&s.izh[a], c);
-        s.gxl[k] = *cl.map_shared_rank(&s.ixl[a], c);
-        s.gyl[k] = *cl.map_shared_rank(&s.iyl[a], c);
-        s.gzl[k] = *cl.map_shared_rank(&s.izl[a], c);
-        s.gvx[k] = *cl.map_shared_rank(&s.ivx[a], c);
-        s.gvy[k] = *cl.map_shared_rank(&s.ivy[a], c);
-        s.gvz[k] = *cl.map_shared_rank(&s.ivz[a], c);
-        s.grow[k] = *cl.map_shared_rank(&s.irow[a], c);
+      if (g0 > 0) {
+        // a later group's i data from its owners' shared memory (the loads
+        // first, then the stores: one round trip)
+        for (int k = tid; k < gn; k += kCT) {
+          const int pos = (int)(g0 + k);
+          int c = 0;
+#pragma unroll
+          for (int cc = 1; cc < kMaxC; ++cc) c += (cc < C && s.cbefore[cc] <= pos) ? 1 : 0;
+          const int a = pos - s.cbefore[c];
+          const float4 A = *cl.map_shared_rank(&s.iA[a], c);
+          const float4 B = *cl.map_shared_rank(&s.iB[a], c);
+          const float2 Ci = *cl.map_shared_rank(&s.iC[a], c);
+          s.gA[k] = A;
+          s.gB[k] = B;
+          s.gC[k] = Ci;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       // own j rows on the group: P threads per particle (a power of two, at
       // most 32, lanes of one warp), each over a contiguous part of the rows
       int P = 32;
       while (P > 1 && P * gn > kCT) P >>= 1;
       const int i = tid / P, part = tid % P;
-      double f[7];
-      {
-        float hi7[7], lo7[7];
+      float hi7[7], lo7[7];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) hi7[c] = lo7[c] = 0.0f;
-        if (i < gn) {
-          const float xh = s.gxh[i], yh = s.gyh[i], zh = s.gzh[i], xl = s.gxl[i], yl = s.gyl[i], zl = s.gzl[i];
-          const float vx = s.gvx[i], vy = s.gvy[i], vz = s.gvz[i];
-          const int self = own_index(s.grow[i], me, C);  // -1: held by another CTA
-          const int q0 = (int)((int64_t)part * nr / P), q1 = (int)((int64_t)(part + 1) * nr / P);
-          for (int c0 = q0; c0 < q1; c0 += kChunk) {
-            const int c1 = min(c0 + kChunk, q1);
-            float pp[7];
+      for (int c = 0; c < 7; ++c) hi7[c] = lo7[c] = 0.0f;
+      if (i < gn) {
+        const float4 A = s.gA[i], B = s.gB[i];
+        const float2 Ci = s.gC[i];
+        const float xh = A.x, yh = A.y, zh = A.z, xl = B.x, yl = B.y, zl = B.z;
+        const float vx = A.w, vy = B.w, vz = Ci.x;
+        const int self = own_index(__float_as_int(Ci.y), me, C);  // -1: held by another CTA
+        const int q0 = (int)((int64_t)part * nr / P), q1 = (int)((int64_t)(part + 1) * nr / P);
+        for (int c0 = q0; c0 < q1; c0 += kChunk) {
+          const int c1 = min(c0 + kChunk, q1);
+          float pp[7];
 #pragma unroll
-            for (int c = 0; c < 7; ++c) pp[c] = 0.0f;
-            for (int q = c0; q < c1; ++q) {
-              const float dx = (s.jxh[q] - xh) + (s.jxl[q] - xl);
-              const float dy = (s.jyh[q] - yh) + (s.jyl[q] - yl);
-              const float dz = (s.jzh[q] - zh) + (s.jzl[q] - zl);
-              const float wx = s.jvx[q] - vx, wy = s.jvy[q] - vy, wz = s.jvz[q] - vz;
-              const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, p.eps2f)));
-              const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
-              float rinv = nb_rsqrt_approx(r2);
-              rinv = (q == self) ? 0.0f : rinv;  // the self pair, by row
-              const float rinv2 = rinv * rinv;
-              const float mr = s.jms[q] * rinv;
-              const float mr3 = mr * rinv2;
-              const float a3 = (rw * -3.0f) * rinv2;  // the jerk term formed before it is added
-              pp[6] += mr;
-              pp[0] = fmaf(mr3, dx, pp[0]);
-              pp[1] = fmaf(mr3, dy, pp[1]);
-              pp[2] = fmaf(mr3, dz, pp[2]);
-              pp[3] = fmaf(mr3, fmaf(a3, dx, wx), pp[3]);
-              pp[4] = fmaf(mr3, fmaf(a3, dy, wy), pp[4]);
-              pp[5] = fmaf(mr3, fmaf(a3, dz, wz), pp[5]);
-            }
-#pragma unroll
-            for (int c = 0; c < 7; ++c) {  // double-single fold (Knuth's TwoSum)
-              const float a_ = hi7[c], b_ = pp[c];
-              const float sum = a_ + b_;
-              const float bb = sum - a_;
-              lo7[c] += (a_ - (sum - bb)) + (b_ - bb);
-              hi7[c] = sum;
-            }
+          for (int c = 0; c < 7; ++c) pp[c] = 0.0f;
+          for (int q = c0; q < c1; ++q) {
+            const float dx = (s.jxh[q] - xh) + (s.jxl[q] - xl);
+            const float dy = (s.jyh[q] - yh) + (s.jyl[q] - yl);
+            const float dz = (s.jzh[q] - zh) + (s.jzl[q] - zl);
+            const float wx = s.jvx[q] - vx, wy = s.jvy[q] - vy, wz = s.jvz[q] - vz;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, p.eps2f)));
+            const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+            float rinv = nb_rsqrt_approx(r2);
+            rinv = (q == self) ? 0.0f : rinv;  // the self pair, by row
+            const float rinv2 = rinv * rinv;
+            const float mr = s.jms[q] * rinv;
+            const float mr3 = mr * rinv2;
+            const float a3 = (rw * -3.0f) * rinv2;  // the jerk term formed before it is added
+            pp[6] += mr;
+            pp[0] = fmaf(mr3, dx, pp[0]);
+            pp[1] = fmaf(mr3, dy, pp[1]);
+            pp[2] = fmaf(mr3, dz, pp[2]);
+            pp[3] = fmaf(mr3, fmaf(a3, dx, wx), pp[3]);
+            pp[4] = fmaf(mr3, fmaf(a3, dy, wy), pp[4]);
+            pp[5] = fmaf(mr3, fmaf(a3, dz, wz), pp[5]);
           }
-        }
 #pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] = (double)hi7[c] + (double)lo7[c];
+          for (int c = 0; c < 7; ++c) ds_add(hi7[c], lo7[c], pp[c], 0.0f);  // double-single fold
+        }
       }
-      // the P parts of a particle, lanes of one warp: butterfly (every lane)
+      // the P parts of a particle, lanes of one warp: a double-single
+      // butterfly in FP32 (every lane; the FP64 pipe is 1/64 of FP32 here)
       for (int o = P / 2; o > 0; o >>= 1)
 #pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
+        for (int c = 0; c < 7; ++c) {
+          const float oh = __shfl_xor_sync(0xffffffffu, hi7[c], o);
+          const float ol = __shfl_xor_sync(0xffffffffu, lo7[c], o);
+          ds_add(hi7[c], lo7[c], oh, ol);
+        }
       if (i < gn && part == 0)
 #pragma unroll
-        for (int c = 0; c < 7; ++c) s.part[c][i] = f[c];
+        for (int c = 0; c < 7; ++c) s.part[c][i] = make_float2(hi7[c], lo7[c]);
       __syncthreads();
       cl.sync();  // C: every CTA's partial sums on the group are ready
 
@@ -348,29 +394,41 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       // the corrector on four lanes per particle (step 5)
       const int lo_pos = max((int)g0, before), hi_pos = min((int)g0 + gn, before + mine);
       const int own = hi_pos - lo_pos;  // CTA-uniform
-      // one thread per (particle, component): the C partials in CTA order
+      // one thread per (particle, component): the C double-single partials
+      // (independent loads, one round trip) summed in CTA order
       for (int e = tid; e < own * 7; e += kCT) {
         const int k = lo_pos - (int)g0 + e / 7, c = e % 7;
-        double acc = 0.0;
-        for (int cc = 0; cc < C; ++cc) acc += *cl.map_shared_rank(&s.part[c][k], cc);
+        float2 pv[kMaxC];
+#pragma unroll
+        for (int cc = 0; cc < kMaxC; ++cc)
+          pv[cc] = cc < C ? *cl.map_shared_rank(&s.part[c][k], cc) : make_float2(0.0f, 0.0f);
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < kMaxC; ++cc)
+          if (cc < C) ds_add(h, l, pv[cc].x, pv[cc].y);
+        const double acc = (double)h + (double)l;
         s.fsum[c][k] = c == 6 ? -acc : acc;
       }
       __syncthreads();
       for (int k0 = 0; k0 < own; k0 += kCT / 4) {
-        const int sub = tid & 3;
+        const int sub = tid & 3, cs = sub < 3 ? sub : 0;
         const int pos = lo_pos + k0 + (tid >> 2);
         const bool have = pos < hi_pos;
         double fo[7];
 #pragma unroll
         for (int c = 0; c < 7; ++c) fo[c] = have ? s.fsum[c][pos - (int)g0] : 0.0;
-        const int64_t row = have ? (int64_t)s.irow[pos - before] : (int64_t)s.irow[lo_pos - before];
-        const double nd = nbh::correct_row_lanes4(row, p.n_pad, tn, fo, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a, p.jk,
-                                                  p.pot, p.t, p.dt, p.xp, p.vp, p.st, sub, (tid & 31) - sub, have);
-        __syncwarp();
-        if (have && sub == 0) {
-          nbh::write_jm_record(row, N, p.n_pad, p.m, p.x, p.v, p.a, p.jk, p.dt, p.jm);
-          s.due[own_index(row, me, C)] = (unsigned long long)__double_as_longlong(nd);
+        const int kk = have ? pos - before : lo_pos - before;  // own active index
+        const int64_t row = s.irow[kk];
+        nbh::CorrIn in;
+        if (kk < kCC) {
+          in = nbh::CorrIn{s.cT[kk], s.cDT[kk], s.cA0[cs][kk], s.cJ0[cs][kk], s.cXP[cs][kk], s.cVP[cs][kk]};
+        } else {
+          const int64_t q = cs * p.n_pad + row;
+          in = nbh::CorrIn{p.t[row], p.dt[row], p.a[q], p.jk[q], p.xp[q], p.vp[q]};
         }
+        const double nd = nbh::correct_lanes4(row, p.n_pad, tn, fo, in, p.eta, p.dt_min, p.dt_max, p.x, p.v, p.a,
+                                              p.jk, p.pot, p.t, p.dt, p.st, sub, (tid & 31) - sub, have, p.jm);
+        if (have && sub == 0) s.due[own_index(row, me, C)] = (unsigned long long)__double_as_longlong(nd);
       }
       __syncthreads();
       if (g0 + kGI < n) cl.sync();  // D: the partials are read before the next group's are written
@@ -381,8 +439,9 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       p.ctl->interactions += n * (long long)N;
     }
     __syncthreads();
-    publish(p, s, me, C, nr);
+    publish(s, cl, me, C, nr);
   }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 struct CLoop {

@@ -146,6 +146,13 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
   return t + dnew;
 }
 
+// Inputs of one lane's part of a correction: the row's time and step before
+// it, and component `sub` (< 3; lane 3 takes component 0) of the old
+// acceleration and jerk and of the predicted position and velocity.
+struct CorrIn {
+  double t0, dt0, a0, j0, xp, vp;
+};
+
 // The same correction spread over four lanes of a warp: lane `sub` < 3 of
 // the group takes component `sub` (the same FP64 operations in the same order
 // as correct_row), the squared norms are gathered by shuffles and summed in
@@ -158,44 +165,61 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
 // shuffles use the full mask and are taken unconditionally.  `base` is the
 // warp lane of the group's lane 0; `write` says whether this group's row is
 // real (lanes of groups without a row, and lanes sub >= 4, compute on a
-// valid row and write nothing).  Returns, on the group's lane 0 of a real
-// row, the row's next due time t + dt_new (0 elsewhere).
-__device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
-                                                   double eta, double dt_min, double dt_max, double* __restrict__ x,
-                                                   double* __restrict__ v, double* __restrict__ a,
-                                                   double* __restrict__ jk, double* __restrict__ pot,
-                                                   double* __restrict__ ti, double* __restrict__ dt,
-                                                   const double* __restrict__ xp, const double* __restrict__ vp,
-                                                   nb_dev_status* __restrict__ st, int sub, int base, bool write) {
-  const double h = t - ti[i];
+// valid row and write nothing).  With jm the corrected row's j-memory record
+// is written as well (write_jm_record's values; its mass word is left as it
+// is): each lane its component, lane 0 the reach once the new step is known.
+// Returns, on the group's lane 0 of a real row, the row's next due time
+// t + dt_new (0 elsewhere).
+__device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
+                                                 const CorrIn& in, double eta, double dt_min, double dt_max,
+                                                 double* __restrict__ x, double* __restrict__ v,
+                                                 double* __restrict__ a, double* __restrict__ jk,
+                                                 double* __restrict__ pot, double* __restrict__ ti,
+                                                 double* __restrict__ dt, nb_dev_status* __restrict__ st, int sub,
+                                                 int base, bool write, float4* __restrict__ jm = nullptr) {
+  const double h = t - in.t0;
   const double ih = div_pow2(1.0, h);
   const double ih2 = ih * ih, ih3 = ih2 * ih;
   const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
   double sq[4] = {0.0, 0.0, 0.0, 0.0};  // a1^2, j1^2, a2e^2, a3^2 of this lane's component
+  double ab[3];                         // |v1|, |a1|, |j1| of this lane's component (the record's reach)
   int fin = 1;
   const int c = sub < 3 ? sub : 0;
   {
     const int64_t q = c * n_pad + i;
-    const double a0 = a[q], j0 = jk[q];
+    const double a0 = in.a0, j0 = in.j0;
     // (selects, not an index: f stays in registers)
     const double a1 = c == 0 ? f[0] : (c == 1 ? f[1] : f[2]);
     const double j1 = c == 0 ? f[3] : (c == 1 ? f[4] : f[5]);
     const double da = a0 - a1;
     const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
     const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
-    const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
-    const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+    const double x1 = in.xp + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
+    const double v1 = in.vp + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
     const double a2e = a2 + a3 * h;
     if (write && sub < 3) {
       x[q] = x1;
       v[q] = v1;
       a[q] = a1;
       jk[q] = j1;
+      if (jm) {
+        float* r = reinterpret_cast<float*>(jm + i);
+        const float xh = __double2float_rn(x1), vh = __double2float_rn(v1);
+        r[c] = xh;
+        r[4 * n_pad + c] = __double2float_rn(x1 - (double)xh);
+        r[8 * n_pad + c] = vh;
+        r[12 * n_pad + c] = __double2float_rn(v1 - (double)vh);
+        r[16 * n_pad + c] = __double2float_rn(0.5 * a1);
+        r[4 * n_pad * (2 + c) + 3] = __double2float_rn(j1 * (1.0 / 6.0));
+      }
     }
     sq[0] = a1 * a1;
     sq[1] = j1 * j1;
     sq[2] = a2e * a2e;
     sq[3] = a3 * a3;
+    ab[0] = fabs(v1);
+    ab[1] = fabs(a1);
+    ab[2] = fabs(j1);
     fin = (isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1)) ? 1 : 0;
   }
   // norms summed in component order on every lane (0 + x^2 + y^2 + z^2, as
@@ -207,6 +231,16 @@ __device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, d
     const double s1 = __shfl_sync(0xffffffffu, sq[r], base + 1);
     const double s2 = __shfl_sync(0xffffffffu, sq[r], base + 2);
     nrm2[r] = ((0.0 + s0) + s1) + s2;
+  }
+  double sum_ab[3] = {0.0, 0.0, 0.0};  // write_jm_record's sums of |v|, |a|, |j| in component order
+  if (jm) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double s0 = __shfl_sync(0xffffffffu, ab[r], base);
+      const double s1 = __shfl_sync(0xffffffffu, ab[r], base + 1);
+      const double s2 = __shfl_sync(0xffffffffu, ab[r], base + 2);
+      sum_ab[r] = ((0.0 + s0) + s1) + s2;
+    }
   }
   const int f0 = __shfl_sync(0xffffffffu, fin, base);
   const int f1 = __shfl_sync(0xffffffffu, fin, base + 1);
@@ -225,7 +259,7 @@ __device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, d
   const double den = nj * n3 + n2 * n2;
   const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
   if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
-  const double dt_old = dt[i];
+  const double dt_old = in.dt0;
   const double cl = clamp_dt(pow2_floor(crit), dt_min, dt_max);
   double dnew;
   if (cl < dt_old) {
@@ -239,7 +273,25 @@ __device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, d
   if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
   ti[i] = t;
   dt[i] = dnew;
+  if (jm) {
+    const double d = dnew;
+    const double rr = d * (sum_ab[0] + d * (0.5 * sum_ab[1] + d * (sum_ab[2] * (1.0 / 6.0))));
+    reinterpret_cast<float*>(jm + n_pad + i)[3] = __double2float_ru(rr * (1.0 + 0x1p-20));
+  }
   return t + dnew;
+}
+
+// correct_lanes4 with its inputs read from the state and the predicted rows
+__device__ __forceinline__ double correct_row_lanes4(int64_t i, int64_t n_pad, double t, const double (&f)[7],
+                                                   double eta, double dt_min, double dt_max, double* __restrict__ x,
+                                                   double* __restrict__ v, double* __restrict__ a,
+                                                   double* __restrict__ jk, double* __restrict__ pot,
+                                                   double* __restrict__ ti, double* __restrict__ dt,
+                                                   const double* __restrict__ xp, const double* __restrict__ vp,
+                                                   nb_dev_status* __restrict__ st, int sub, int base, bool write) {
+  const int64_t q = (sub < 3 ? sub : 0) * n_pad + i;
+  const CorrIn in{ti[i], dt[i], a[q], jk[q], xp[q], vp[q]};
+  return correct_lanes4(i, n_pad, t, f, in, eta, dt_min, dt_max, x, v, a, jk, pot, ti, dt, st, sub, base, write);
 }
 
 // j-memory record of row i (the on-the-fly j prediction's input, Sec. 4.4
