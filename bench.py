@@ -467,13 +467,13 @@ def run_integration(args):
                 d_act = torch.from_numpy(act).cuda()
                 tuned = None
                 if name == "mixed_autotuned":
-                    # nb_autotune on this block (its trial launches use the first n particles of
+                    # nb_autotune_list on this block (the trial launches use this active list on
                     # the same state), then the same timed calls take the tuned launch; with
                     # --tune-file the table collects every n's entry
                     if args.tune_file and os.path.exists(args.tune_file):
                         s.tune_load(args.tune_file)
                     s.predict(T)
-                    tuned = s.autotune(n)
+                    tuned = s.autotune_list(d_act)
                     if args.tune_file:
                         s.tune_save(args.tune_file)
                 A = torch.empty((n, 3), dtype=torch.float64, device="cuda")

@@ -391,9 +391,10 @@ int nb_set_tuning(nb_ctx* ctx, int i_per_thread, int threads, int j_tile, int n_
 
 /*
  * nb_set_far_tiles -- the mixed path's far-tile pass (not in the paper).
- * With the particles kept in spatial order, a (warp of i, j-tile) pair whose
- * bounding boxes are at least theta (|x|max_i + |x|max_j) apart (theta = 1/8)
- * forms each position difference from the FP32 "hi" parts alone, with
+ * With the particles kept in spatial order, a (warp of i, j-tile) pair in
+ * which every i of the warp is at least theta (|x_i| + |x|max_j) from the
+ * tile's bounding box (theta = 1/8) forms each position difference from the
+ * FP32 "hi" parts alone, with
  * relative error <= 2^-24 (1/theta + 1) ~ 5.4e-7 per pair; every other pair,
  * and every pair when the pass is off, uses the double-single difference
  * (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo).  enable != 0 turns the pass on (the
@@ -417,6 +418,20 @@ int nb_get_far_tiles(nb_ctx* ctx, int* enabled);
  * pointer may be NULL; *n_split = 0 means the automatic split).
  */
 int nb_autotune(nb_ctx* ctx, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split);
+
+/*
+ * nb_autotune_list -- nb_autotune timed on the caller's active list (n
+ * particle indices, ascending, in host or device memory per ptr_kind) instead
+ * of the first n particles of the resident spatial order, so that the launch
+ * shapes are compared on the block that will run: a block scattered over the
+ * system finds fewer far tiles than a compact one and favours other shapes.
+ * The entry is kept for (N, n) like nb_autotune's.  Errors: NB_EINVAL (n out
+ * of [1, N], NULL list, bad ptr_kind; a device list that is not ascending is
+ * reported as NB_EINVAL by the next call that checks the status word),
+ * NB_ESTATE (no prediction), NB_ECUDA.
+ */
+int nb_autotune_list(nb_ctx* ctx, const int32_t* i_idx, int64_t n, int ptr_kind, int* i_per_thread, int* threads,
+                     int* j_tile, int* n_split);
 
 /*
  * nb_ensemble_autotune -- the item shape of the device-driven block steps

@@ -206,6 +206,10 @@ int ensure_sorted(nb_ctx* c) {
 
 // a caller's list on the device, as slots of the resident order
 int caller_list(nb_ctx* c, const int32_t* list, int64_t n, int ptr_kind, const int32_t** d_slots) {
+  if (ptr_kind == NB_PTR_DEVICE) {  // checked and mapped in one launch
+    NB_CUDA(c, nb_check_map_to_slots(c, list, n, d_slots));
+    return NB_OK;
+  }
   const int32_t* d_list = nullptr;
   int r = stage_list(c, list, n, ptr_kind, &d_list);
   if (r) return r;
@@ -323,7 +327,32 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
 }
 
 // the force rows of the last call to the caller (host copies complete on return)
+// a force call's device outputs, written by the split reduction when there
+// is one; they are cleared when the call returns, on every path
+void set_device_outputs(nb_ctx* c, double* acc, double* jerk, double* pot, int ptr_kind) {
+  const bool dev = ptr_kind == NB_PTR_DEVICE;
+  c->fo_acc = dev ? acc : nullptr;
+  c->fo_jerk = dev ? jerk : nullptr;
+  c->fo_pot = dev ? pot : nullptr;
+  c->fo_done = false;
+}
+
+struct DeviceOutputsScope {
+  nb_ctx* c;
+  ~DeviceOutputsScope() {
+    c->fo_acc = c->fo_jerk = c->fo_pot = nullptr;
+    c->fo_done = false;
+  }
+};
+
 int copy_forces_out(nb_ctx* c, int64_t n, double* acc, double* jerk, double* pot, int ptr_kind) {
+  if (ptr_kind == NB_PTR_DEVICE) {  // one launch (none when the split reduction wrote them)
+    const bool done = c->fo_done;
+    c->fo_acc = c->fo_jerk = c->fo_pot = nullptr;
+    c->fo_done = false;
+    if (!done && (acc || jerk || pot)) NB_CUDA(c, nb_launch_forces_out(c, n, acc, jerk, pot, 0));
+    return NB_OK;
+  }
   int r;
   for (int q = 0; q < 2; ++q) {
     double* dst = q == 0 ? acc : jerk;
@@ -604,6 +633,8 @@ int nb_compute_forces(nb_ctx* c, const int32_t* i_idx, int64_t n, double* acc, d
   const int32_t* d_list = nullptr;
   int r = caller_list(c, i_idx, n, ptr_kind, &d_list);
   if (r) return r;
+  set_device_outputs(c, acc, jerk, pot, ptr_kind);
+  const DeviceOutputsScope fo_scope{c};
   NB_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
   NB_CUDA(c, nb_forces(c, d_list, n));
   NB_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
@@ -629,6 +660,8 @@ int nb_compute_forces_at(nb_ctx* c, double t, const int32_t* i_idx, int64_t n, d
   if (r) return r;
   const int32_t* d_list = nullptr;
   if ((r = caller_list(c, i_idx, n, ptr_kind, &d_list))) return r;
+  set_device_outputs(c, acc, jerk, pot, ptr_kind);
+  const DeviceOutputsScope fo_scope{c};
   NB_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
   if (c->precision == NB_MIXED) {
     if ((r = nb_jm_ensure(c))) return fail(c, r);
@@ -1046,10 +1079,13 @@ int nb_get_far_tiles(nb_ctx* c, int* enabled) {
   return NB_OK;
 }
 
-int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split) {
-  NB_SINGLE(c);
-  if (n < 1 || n > c->n) return fail(c, NB_EINVAL);
-  if (!c->pred_valid) return fail(c, NB_ESTATE);
+}  // extern "C"
+
+namespace {
+
+// the autotuner's search on the device slot list d_slots (n entries)
+int autotune_on(nb_ctx* c, const int32_t* d_slots, int64_t n, int* i_per_thread, int* threads, int* j_tile,
+                int* n_split) {
   static const int thr_list[] = {64, 128, 256};
   static const int ipt_mixed[] = {1, 2, 4};
   static const int jt_mixed[] = {64, 128, 256};
@@ -1063,28 +1099,41 @@ int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_ti
         nb_tuning cfg{c->precision == NB_MIXED ? ipt_mixed[ii] : 1, thr_list[ti],
                       c->precision == NB_MIXED ? jt_mixed[ji] : jt_fp64[ji], 0};
         if (!nb_tuning_supported(c->precision, cfg)) continue;
-        // the automatic split (0, sized from the kernel's occupancy) and a
-        // smaller and a larger explicit one
+        // the automatic split (0, sized from the kernel's occupancy), a
+        // smaller and a larger explicit one, and (mixed) the splits that fill
+        // exactly one and two waves of resident CTAs
         const int guess = nb_auto_split(c, n, cfg, 4);
-        const int splits[] = {0, std::max(1, guess / 2), guess * 2};
+        int splits[5] = {0, std::max(1, guess / 2), guess * 2, 0, 0};
+        const int64_t itiles = (n + (int64_t)cfg.threads * cfg.ipt - 1) / ((int64_t)cfg.threads * cfg.ipt);
+        const int per_sm = c->precision == NB_MIXED ? nb_mixed_ctas_per_sm(cfg) : 0;
+        if (per_sm > 0 && guess > 1) {
+          const int64_t R = (int64_t)c->sm_count * per_sm;
+          for (int w = 1; w <= 2; ++w)
+            if (w * R >= 2 * itiles) splits[2 + w] = (int)std::min<int64_t>(4096, w * R / itiles);
+        }
         // explicit splits beyond the partial-sum scratch (or the supported
         // maximum) cannot launch: not candidates
         const int64_t cap = std::min<int64_t>(4096, c->part_elems / (7 * (((n + 31) / 32) * 32)));
-        for (int si = 0; si < 3; ++si) {
-          if (si > 0 && (guess == 1 || splits[si] == splits[si - 1] || splits[si] > cap)) continue;
+        for (int si = 0; si < 5; ++si) {
+          if (si > 0) {
+            if (guess == 1 || splits[si] < 1 || splits[si] > cap) continue;
+            bool seen = false;
+            for (int sj = 1; sj < si; ++sj) seen = seen || splits[sj] == splits[si];
+            if (seen) continue;
+          }
           nb_tuning t = cfg;
           t.nsplit = splits[si];
           c->tune_override = t;
-          NB_CUDA(c, nb_forces(c, c->ident, n));  // warm-up
+          NB_CUDA(c, nb_forces(c, d_slots, n));  // warm-up
           NB_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
-          NB_CUDA(c, nb_forces(c, c->ident, n));
+          NB_CUDA(c, nb_forces(c, d_slots, n));
           NB_CUDA(c, cudaEventRecord(c->ev[7], c->stream));
           NB_CUDA(c, cudaStreamSynchronize(c->stream));
           float ms = elapsed(c->ev[6], c->ev[7]);
           if (ms < 5.0f) {  // short launches: average a few more
             const int reps = 5;
             NB_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
-            for (int r = 0; r < reps; ++r) NB_CUDA(c, nb_forces(c, c->ident, n));
+            for (int r = 0; r < reps; ++r) NB_CUDA(c, nb_forces(c, d_slots, n));
             NB_CUDA(c, cudaEventRecord(c->ev[7], c->stream));
             NB_CUDA(c, cudaStreamSynchronize(c->stream));
             ms = elapsed(c->ev[6], c->ev[7]) / reps;
@@ -1107,6 +1156,29 @@ int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_ti
   if (j_tile) *j_tile = best.jtile;
   if (n_split) *n_split = best.nsplit;
   return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nb_autotune(nb_ctx* c, int64_t n, int* i_per_thread, int* threads, int* j_tile, int* n_split) {
+  NB_SINGLE(c);
+  if (n < 1 || n > c->n) return fail(c, NB_EINVAL);
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  return autotune_on(c, c->ident, n, i_per_thread, threads, j_tile, n_split);
+}
+
+int nb_autotune_list(nb_ctx* c, const int32_t* i_idx, int64_t n, int ptr_kind, int* i_per_thread, int* threads,
+                     int* j_tile, int* n_split) {
+  NB_SINGLE(c);
+  if (n < 1 || n > c->n || !i_idx) return fail(c, NB_EINVAL);
+  if (ptr_kind != NB_PTR_HOST && ptr_kind != NB_PTR_DEVICE) return fail(c, NB_EINVAL);
+  if (!c->pred_valid) return fail(c, NB_ESTATE);
+  const int32_t* d_slots = nullptr;
+  const int r = caller_list(c, i_idx, n, ptr_kind, &d_slots);
+  if (r) return r;
+  return autotune_on(c, d_slots, n, i_per_thread, threads, j_tile, n_split);
 }
 
 }  // extern "C"

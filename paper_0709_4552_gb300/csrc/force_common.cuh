@@ -429,6 +429,12 @@ __device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const flo
   }
 }
 
+// an FP64 value as a double-single pair: hi = fl32(x), lo = fl32(x - hi)
+__device__ __forceinline__ float2 ds_split(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
 // Mixed-precision item: i-tile starting at list position ibase (n entries in
 // list, entries clamped to [0, idx_hi)), j-range [jlo, jhi).  Writes 7 rows
 // out[c * ostride + pos] (final: acc, jerk, pot with its sign) or raw sums.
@@ -442,7 +448,8 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
                                            float eps2, double* __restrict__ out, int64_t ostride,
                                            bool finalize, const float4* __restrict__ tbox = nullptr,
                                            const int32_t* __restrict__ ord = nullptr, int64_t box_origin = 0,
-                                           const FusedArgs fa = FusedArgs(), const ISrc is = ISrc()) {
+                                           const FusedArgs fa = FusedArgs(), const ISrc is = ISrc(),
+                                           bool ds_out = false) {
   constexpr bool kFusedLoad = SM::kFused;
   // list: j-store slots of the i-particles.  ord (optional): the list
   // positions in processing order (a caller's list visited in spatial
@@ -475,10 +482,12 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
     acc_hi[k][c] = s_;                                          \
   } while (0)
 #define NB_ACC_GET(k, c) ((double)acc_hi[k][c] + (double)acc_lo[k][c])
+#define NB_ACC_DS(k, c) make_float2(acc_hi[k][c], acc_lo[k][c])
 #else
 #define NB_ACC_ZERO(k, c) (NB_ACC(k, c) = 0.0)
 #define NB_ACC_ADD(k, c, val) (NB_ACC(k, c) += (double)(val))
 #define NB_ACC_GET(k, c) NB_ACC(k, c)
+#define NB_ACC_DS(k, c) ds_split(NB_ACC(k, c))
 #endif
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
@@ -654,19 +663,31 @@ __device__ __forceinline__ void mixed_item(SM& sm, const float4* __restrict__ jA
   }
   cp_async_wait<0>();
 
+  // final results (one split): FP64 with the potential's sign; partial sums
+  // of a split: FP64, or with ds_out the double-single pair (hi, lo) in the
+  // same 8-byte slot (no FP64 instruction: the FP64 pipe issues a warp
+  // instruction every 64 cycles per warp on this GPU), which the split
+  // reduction sums in FP32 (split_reduce_ds)
+  float2* out2 = reinterpret_cast<float2*>(out);
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     int64_t pos = ibase + k * NT + tid;
     if (pos >= n) continue;
     if (ord) pos = ord[pos];
+    if (ds_out && !finalize) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) out[c * ostride + pos] = NB_ACC_GET(k, c);
-    out[6 * ostride + pos] = finalize ? -NB_ACC_GET(k, 6) : NB_ACC_GET(k, 6);
+      for (int c = 0; c < 7; ++c) out2[c * ostride + pos] = NB_ACC_DS(k, c);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) out[c * ostride + pos] = NB_ACC_GET(k, c);
+      out[6 * ostride + pos] = finalize ? -NB_ACC_GET(k, 6) : NB_ACC_GET(k, 6);
+    }
   }
 #undef NB_ACC
 #undef NB_ACC_ZERO
 #undef NB_ACC_ADD
 #undef NB_ACC_GET
+#undef NB_ACC_DS
 }
 
 template <int JT>

@@ -40,8 +40,19 @@ __global__ void split_reduce_kernel(const double* __restrict__ part, int64_t str
   for (int64_t k0 = (int64_t)blockIdx.x * 32; k0 < n; k0 += (int64_t)gridDim.x * 32) {
     const int64_t k = k0 + tx;
     double s = 0.0;
-    if (k < n)
-      for (int q = ty; q < nsplit; q += QL) s += part[((int64_t)q * 7 + c) * stride + k];
+    if (k < n) {
+      // splits ty, ty + QL, ... added in order, loaded 8 at a time (one
+      // round trip per batch instead of per split)
+      int q = ty;
+      for (; q + 7 * QL < nsplit; q += 8 * QL) {
+        double v[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) v[b] = part[((int64_t)(q + b * QL) * 7 + c) * stride + k];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) s += v[b];
+      }
+      for (; q < nsplit; q += QL) s += part[((int64_t)q * 7 + c) * stride + k];
+    }
     sm[ty][tx] = s;
     __syncthreads();
 #pragma unroll

@@ -2,9 +2,10 @@
 // (force_common.cuh; Sec. 4.1 step 4, Eq. 3) for sm_103a.
 //
 // Grid: (i-tiles of NT*IPT active particles) x (j-range splits).  With one
-// split the item writes final results into F; otherwise FP64 partials
-// [split][7][n] that the split-j reduction sums in a fixed order
-// (deterministic for a given launch configuration).
+// split the item writes final results into F; otherwise double-single
+// partials [split][7][n] (an FP32 pair per 8-byte slot) that the split-j
+// reduction sums in FP32, in a fixed order (deterministic for a given launch
+// configuration), and converts to FP64 once per result.
 #include "force_common.cuh"
 
 namespace {
@@ -32,7 +33,7 @@ __global__ void NB_MIXED_BOUNDS(NT, IPT) force_mixed_kernel(
   const int64_t jhi = min(nbk::split_begin(split + 1, gridDim.y, tiles) * JT, n_j);
   double* o = finalize ? out : out + (int64_t)split * 7 * ostride;
   nbk::mixed_item<NT, IPT, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * (NT * IPT),
-                               eps2, o, ostride, finalize != 0, tbox, ord, 0, nbk::FusedArgs(), is);
+                               eps2, o, ostride, finalize != 0, tbox, ord, 0, nbk::FusedArgs(), is, true);
 }
 
 // the same item with on-the-fly prediction of the j-tiles from the j-memory
@@ -55,16 +56,96 @@ __global__ void __launch_bounds__(NT) force_mixed_fused_kernel(
   fa.tj = tj;
   fa.T = T;
   nbk::mixed_item<NT, 1, JT>(sm, jA, jB, jC, jlo, jhi, n_j, list, n, (int64_t)blockIdx.x * NT, eps2, o, ostride,
-                             finalize != 0, tbox, ord, 0, fa);
+                             finalize != 0, tbox, ord, 0, fa, nbk::ISrc(), true);
+}
+
+// (hi, lo) += (bh, bl): double-single sum (Knuth's TwoSum of the high parts,
+// the low parts and the rounding error added without renormalisation)
+__device__ __forceinline__ void ds_acc(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  lo = (lo + bl) + ((hi - (s - bb)) + (bh - bb));
+  hi = s;
+}
+
+// Split-j reduction of double-single partials: CTA (32 x kQL threads) =
+// 32 consecutive list positions (coalesced rows) x kQL lanes over the
+// splits; lane ty sums splits ty, ty + kQL, ... in order (loads in batches of
+// kB, so that a thread waits for one round trip per batch), then a fixed
+// pairwise tree over ty; one FP64 conversion per result.  Also writes the
+// caller's AoS outputs when given.
+constexpr int kQL = 32, kB = 8;
+__global__ void __launch_bounds__(32 * kQL) split_reduce_ds_kernel(const float2* __restrict__ part, int64_t stride,
+                                                                  int nsplit, int64_t n, double* __restrict__ F,
+                                                                  int64_t fstride, double* __restrict__ acc,
+                                                                  double* __restrict__ jerk,
+                                                                  double* __restrict__ pot) {
+  __shared__ float2 sm[kQL][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.y;
+  for (int64_t k0 = (int64_t)blockIdx.x * 32; k0 < n; k0 += (int64_t)gridDim.x * 32) {
+    const int64_t k = k0 + tx;
+    float hi = 0.0f, lo = 0.0f;
+    if (k < n) {
+      const float2* src = part + (int64_t)c * stride + k;
+      const int64_t step = (int64_t)kQL * 7 * stride;  // kQL splits further on
+      int q = ty;
+      for (; q + (kB - 1) * kQL < nsplit; q += kB * kQL) {
+        float2 v[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) v[b] = src[(int64_t)q * 7 * stride + b * step];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) ds_acc(hi, lo, v[b].x, v[b].y);
+      }
+      for (; q < nsplit; q += kQL) {
+        const float2 v = src[(int64_t)q * 7 * stride];
+        ds_acc(hi, lo, v.x, v.y);
+      }
+    }
+    sm[ty][tx] = make_float2(hi, lo);
+    __syncthreads();
+#pragma unroll
+    for (int h = kQL / 2; h > 0; h >>= 1) {
+      if (ty < h) {
+        float2 a = sm[ty][tx];
+        const float2 b = sm[ty + h][tx];
+        ds_acc(a.x, a.y, b.x, b.y);
+        sm[ty][tx] = a;
+      }
+      __syncthreads();
+    }
+    if (ty == 0 && k < n) {
+      const double s = (double)sm[0][tx].x + (double)sm[0][tx].y;
+      const double val = c == 6 ? -s : s;
+      F[c * fstride + k] = val;
+      if (c < 3) {
+        if (acc) acc[3 * k + c] = val;
+      } else if (c < 6) {
+        if (jerk) jerk[3 * k + (c - 3)] = val;
+      } else if (pot) {
+        pot[k] = val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// resident CTAs per SM of an instantiation (0 when the query fails)
+template <int NT, int IPT, int JT>
+int per_sm_of() {
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_mixed_kernel<NT, IPT, JT>, NT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 0;
+  }
+  return per_sm;
 }
 
 template <int NT, int IPT, int JT>
 cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning& cfg, float eps2,
                    const int32_t* ord, const nbk::ISrc& is) {
-  static int per_sm = 0;  // resident CTAs per SM of this instantiation
-  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, force_mixed_kernel<NT, IPT, JT>, NT,
-                                                                   0) != cudaSuccess)
-    return cudaGetLastError();
+  const int per_sm = per_sm_of<NT, IPT, JT>();
+  if (per_sm == 0) return cudaErrorInvalidValue;
   int nsplit = cfg.nsplit > 0 ? cfg.nsplit : nb_auto_split(c, n, cfg, per_sm);
   const int64_t per_cta = (int64_t)NT * IPT;
   const int64_t itiles = (n + per_cta - 1) / per_cta;
@@ -85,7 +166,7 @@ cudaError_t launch(nb_ctx* c, const int32_t* d_list, int64_t n, const nb_tuning&
                                                               eps2, out, ostride, fin ? 1 : 0, tbox, ord, is);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
-  return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
+  return nb_launch_split_reduce_ds(c, n, nsplit, ostride);
 }
 
 }  // namespace
@@ -119,7 +200,31 @@ cudaError_t nb_forces_mixed_fused(nb_ctx* c, const int32_t* d_list, int64_t n, c
       c->t, T);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || fin) return e;
-  return nb_launch_split_reduce(c, d_list, n, nsplit, ostride);
+  return nb_launch_split_reduce_ds(c, n, nsplit, ostride);
+}
+
+cudaError_t nb_launch_split_reduce_ds(nb_ctx* c, int64_t n, int nsplit, int64_t stride) {
+  int64_t g = (n + 31) / 32;
+  if (g > (int64_t)c->sm_count * 4) g = (int64_t)c->sm_count * 4;
+  if (g < 1) g = 1;
+  split_reduce_ds_kernel<<<dim3((unsigned)g, 7), dim3(32, kQL), 0, c->stream>>>(
+      reinterpret_cast<const float2*>(c->part), stride, nsplit, n, c->F, c->n_pad, c->fo_acc, c->fo_jerk, c->fo_pot);
+  if (c->fo_acc || c->fo_jerk || c->fo_pot) c->fo_done = true;
+  return cudaGetLastError();
+}
+
+int nb_mixed_ctas_per_sm(const nb_tuning& cfg) {
+#define NB_PER_SM_CASE(NT_, IPT_, JT_) \
+  if (cfg.threads == NT_ && cfg.ipt == IPT_ && cfg.jtile == JT_) return per_sm_of<NT_, IPT_, JT_>();
+#define NB_PER_SM_JT(NT_, IPT_) NB_PER_SM_CASE(NT_, IPT_, 64) NB_PER_SM_CASE(NT_, IPT_, 128) NB_PER_SM_CASE(NT_, IPT_, 256)
+#define NB_PER_SM_IPT(NT_) NB_PER_SM_JT(NT_, 1) NB_PER_SM_JT(NT_, 2) NB_PER_SM_JT(NT_, 4)
+  NB_PER_SM_IPT(64)
+  NB_PER_SM_IPT(128)
+  NB_PER_SM_IPT(256)
+#undef NB_PER_SM_IPT
+#undef NB_PER_SM_JT
+#undef NB_PER_SM_CASE
+  return 0;
 }
 
 bool nb_mixed_supported(const nb_tuning& t) {

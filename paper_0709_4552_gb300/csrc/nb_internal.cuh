@@ -144,6 +144,10 @@ struct nb_ctx {
   int32_t *ext_self, *ext_ident;
   int64_t* ext_gid;          // staged global ids of a host block
   int64_t ext_cap;
+  // a caller's device outputs of the current force call (AoS acc, jerk and
+  // pot, any NULL): the split reduction writes them beside F and sets fo_done
+  double *fo_acc, *fo_jerk, *fo_pot;
+  bool fo_done;
   // tuning
   nb_tuning tune_override;   // all-zero = automatic
   nb_tune_entry tune_table[NB_TUNE_MAX];
@@ -217,8 +221,13 @@ cudaError_t nb_forces_mixed_fused(nb_ctx* c, const int32_t* d_list, int64_t n, c
 // split-j reduction (force_fp64.cu): part[S][7][n] -> F in fixed order, potential sign
 cudaError_t nb_launch_split_reduce(nb_ctx* c, const int32_t* d_list, int64_t n, int nsplit,
                                    int64_t stride);
+// the same for double-single partials (float2 in each 8-byte slot, force_mixed.cu),
+// summed in FP32; also writes the caller's device outputs c->fo_* when set
+cudaError_t nb_launch_split_reduce_ds(nb_ctx* c, int64_t n, int nsplit, int64_t stride);
 bool nb_tuning_supported(int precision, const nb_tuning& cfg);
 nb_tuning nb_default_tuning(int precision);
+// resident CTAs per SM of the mixed launch of shape cfg (0 = unsupported)
+int nb_mixed_ctas_per_sm(const nb_tuning& cfg);
 // split-j factor for a kernel with per_sm resident CTAs per SM
 int nb_auto_split(const nb_ctx* c, int64_t n, const nb_tuning& cfg, int per_sm);
 
@@ -232,6 +241,9 @@ cudaError_t nb_order_rows_by_keys(nb_ctx* c, int bits);
 cudaError_t nb_unsort(nb_ctx* c);             // back to particle order (perm_valid = false)
 // caller list of particles -> list of slots in c->mlist (*out = d_list when unsorted)
 cudaError_t nb_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out);
+// a caller's device list checked (ascending, in [0, N): else NB_ST_BADLIST) and
+// mapped to slots in one launch (*out = c->mlist, or d_list when unsorted)
+cudaError_t nb_check_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out);
 // slots -> particles: out[k] = perm[in[k]] (in == out allowed)
 cudaError_t nb_map_to_particles(nb_ctx* c, const int32_t* in, int64_t n, int32_t* out);
 // rows of particles [first, first + count) of a state array (rows x n_pad) to AoS dst

@@ -272,6 +272,20 @@ __global__ void map_list(const int32_t* in, int64_t n, const int32_t* __restrict
   }
 }
 
+// a caller's list: NB_ST_BADLIST unless ascending within [0, N); with map,
+// out[k] = map[in[k]] (in[k] clamped to [0, N))
+__global__ void check_map_list(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ map, int64_t N,
+                               int32_t* __restrict__ out, unsigned int* __restrict__ flag) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = in[k];
+    if (v < 0 || v >= N || (k > 0 && in[k - 1] >= v)) atomicOr(flag, NB_ST_BADLIST);
+    if (map) {
+      const int64_t p = v < 0 ? 0 : (v >= N ? N - 1 : v);
+      out[k] = map[p];
+    }
+  }
+}
+
 // dst[k * rows + r] = src[r * n_pad + iperm[first + k]]
 __global__ void gather_rows(const double* __restrict__ src, int rows, int64_t n_pad, const int32_t* __restrict__ iperm,
                             int64_t first, int64_t count, double* __restrict__ dst) {
@@ -374,6 +388,18 @@ cudaError_t nb_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const i
   map_list<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(d_list, n, c->iperm, c->n, c->mlist);
   c->launches += 1;
   *out = c->mlist;
+  return cudaGetLastError();
+}
+
+cudaError_t nb_check_map_to_slots(nb_ctx* c, const int32_t* d_list, int64_t n, const int32_t** out) {
+  if (n <= 0) {
+    *out = d_list;
+    return cudaSuccess;
+  }
+  c->launches += 1;
+  check_map_list<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
+      d_list, n, c->perm_valid ? c->iperm : nullptr, c->n, c->perm_valid ? c->mlist : nullptr, &c->status->flags);
+  *out = c->perm_valid ? c->mlist : d_list;
   return cudaGetLastError();
 }
 

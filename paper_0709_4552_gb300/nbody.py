@@ -39,7 +39,7 @@ EXPORTS = (
     "nb_get_predicted", "nb_forces_on", "nb_set_forces", "nb_set_initial_forces", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
-    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
+    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_autotune_list", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
     "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
@@ -111,6 +111,7 @@ def lib():
         "nb_set_far_tiles": (_int, [_vp, _int]),
         "nb_get_far_tiles": (_int, [_vp, _pint]),
         "nb_autotune": (_int, [_vp, _i64, _pint, _pint, _pint, _pint]),
+        "nb_autotune_list": (_int, [_vp, _vp, _i64, _int, _pint, _pint, _pint, _pint]),
         "nb_ensemble_autotune": (_int, [_vp, _i64, _pint, _pint, _pd, _pd]),
         "nb_tune_save": (_int, [_vp, ctypes.c_char_p]),
         "nb_tune_load": (_int, [_vp, ctypes.c_char_p]),
@@ -461,6 +462,15 @@ def nb_get_far_tiles(ctx):
 def nb_autotune(ctx, n):
     v = [_int() for _ in range(4)]
     _check(lib().nb_autotune(ctx, int(n), *[ctypes.byref(x) for x in v]), "nb_autotune")
+    return dict(i_per_thread=v[0].value, threads=v[1].value, j_tile=v[2].value, n_split=v[3].value)
+
+
+def nb_autotune_list(ctx, i_idx):
+    """nb_autotune timed on the active list i_idx (host or device)."""
+    v = [_int() for _ in range(4)]
+    n = int(i_idx.shape[0])
+    kind, p, keep = _marshal([i_idx], [np.int32])
+    _check(lib().nb_autotune_list(ctx, p[0], n, kind, *[ctypes.byref(x) for x in v]), "nb_autotune_list")
     return dict(i_per_thread=v[0].value, threads=v[1].value, j_tile=v[2].value, n_split=v[3].value)
 
 

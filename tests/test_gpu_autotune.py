@@ -65,6 +65,37 @@ def test_table_file_round_trip(nbl, tmp_path, monkeypatch):
         assert s.tune_count() == 1
 
 
+def test_autotune_on_a_caller_list(nbl, monkeypatch):
+    # nb_autotune_list times the shapes on the caller's (scattered) block; the
+    # entry lands in the table and the tuned forces on that block match the oracle
+    monkeypatch.setenv("NB_TUNE_FILE", "")
+    torch = pytest.importorskip("torch")
+    N, n, eps = 20000, 300, 1.0 / 256
+    m, x, v = inputs.plummer(N, 52)
+    idx = inputs.sample_indices(N, n, 9).astype(np.int32)
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        s.predict(0.0)
+        for lst in (idx, torch.from_numpy(idx).cuda()):   # host and device lists
+            cfg = s.autotune_list(lst)
+            assert cfg["threads"] in (64, 128, 256) and cfg["j_tile"] in (64, 128, 256)
+            assert cfg["i_per_thread"] in (1, 2, 4) and 0 <= cfg["n_split"] <= 4096
+        assert s.tune_count() == 1   # the same (N, n) bin, replaced
+        a, j, p = s.compute_forces(idx)
+    ref = oracle.forces(m, x, v, eps, idx=idx.astype(np.int64), compensated=True)
+    ea = np.linalg.norm(a - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+    ej = np.linalg.norm(j - ref[1], axis=1) / np.linalg.norm(ref[1], axis=1)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+    assert np.median(ej) <= 1e-6 and ej.max() <= 1e-5
+    assert np.abs(p - ref[2]).max() / np.abs(ref[2]).min() <= 1e-5
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:   # a list out of order is refused
+        s.set_j_particles(0, m, x, v)
+        s.predict(0.0)
+        with pytest.raises(nbl.NBodyError):
+            s.autotune_list(idx[::-1].copy())
+
+
 def test_table_refuses_foreign_or_broken_files(nbl, tmp_path, monkeypatch):
     monkeypatch.setenv("NB_TUNE_FILE", "")
     with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
