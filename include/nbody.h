@@ -409,6 +409,19 @@ int nb_set_far_tiles(nb_ctx* ctx, int enable);
 int nb_get_far_tiles(nb_ctx* ctx, int* enabled);
 
 /*
+ * nb_selftest_corrector -- device self-check of the corrector's exact
+ * shortcuts (Sec. 4.1 step 5): the powers of a power-of-two step and the
+ * power-of-two step rule taken from exponent bits instead of FP64 products,
+ * division and square root.  On `samples` seeded random operand sets (steps,
+ * norms, times, step bounds; boundary, zero, subnormal, infinite and NaN
+ * cases included) each shortcut is compared bit for bit with its FP64
+ * expression on `device`; *mismatches receives the number of differences
+ * (0 expected).  Errors: NB_EINVAL (samples < 0, NULL output), NB_ENOMEM,
+ * NB_ECUDA.
+ */
+int nb_selftest_corrector(int device, int64_t samples, uint64_t seed, int64_t* mismatches);
+
+/*
  * nb_autotune -- time the supported force launches of the host-driven path
  * (i per thread, threads per CTA, j-tile, split-j factor) for the current N
  * and active-block size n on the current state (needs a prediction) and keep

@@ -67,16 +67,6 @@ __device__ __forceinline__ int own_count(int64_t N, int me, int C) {
   return (int)((mine - 1) * kRB + min((int64_t)kRB, N - last * kRB));
 }
 
-// (hi, lo) += (bh, bl): double-single sum (Knuth's TwoSum of the high parts,
-// the low parts and the rounding error added without renormalisation, as the
-// force item's fold)
-__device__ __forceinline__ void ds_add(float& hi, float& lo, float bh, float bl) {
-  const float s = hi + bh;
-  const float bb = s - hi;
-  lo = (lo + bl) + ((hi - (s - bb)) + (bh - bb));
-  hi = s;
-}
-
 struct ClusterCtl {
   long long steps;
   long long interactions;
@@ -372,7 +362,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
             pp[5] = fmaf(mr3, fmaf(a3, dz, wz), pp[5]);
           }
 #pragma unroll
-          for (int c = 0; c < 7; ++c) ds_add(hi7[c], lo7[c], pp[c], 0.0f);  // double-single fold
+          for (int c = 0; c < 7; ++c) nbk::ds_add(hi7[c], lo7[c], pp[c], 0.0f);  // double-single fold
         }
       }
       // the P parts of a particle, lanes of one warp: a double-single
@@ -382,7 +372,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
         for (int c = 0; c < 7; ++c) {
           const float oh = __shfl_xor_sync(0xffffffffu, hi7[c], o);
           const float ol = __shfl_xor_sync(0xffffffffu, lo7[c], o);
-          ds_add(hi7[c], lo7[c], oh, ol);
+          nbk::ds_add(hi7[c], lo7[c], oh, ol);
         }
       if (i < gn && part == 0)
 #pragma unroll
@@ -405,7 +395,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
         float h = 0.0f, l = 0.0f;
 #pragma unroll
         for (int cc = 0; cc < kMaxC; ++cc)
-          if (cc < C) ds_add(h, l, pv[cc].x, pv[cc].y);
+          if (cc < C) nbk::ds_add(h, l, pv[cc].x, pv[cc].y);
         const double acc = (double)h + (double)l;
         s.fsum[c][k] = c == 6 ? -acc : acc;
       }

@@ -429,6 +429,16 @@ __device__ __forceinline__ void mixed_pair_pass(const PairTile<JT>& t, const flo
   }
 }
 
+// (hi, lo) += (bh, bl): double-single sum (Knuth's TwoSum of the high parts,
+// the low parts and the rounding error added without renormalisation, as the
+// items' per-tile fold)
+__device__ __forceinline__ void ds_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  lo = (lo + bl) + ((hi - (s - bb)) + (bh - bb));
+  hi = s;
+}
+
 // an FP64 value as a double-single pair: hi = fl32(x), lo = fl32(x - hi)
 __device__ __forceinline__ float2 ds_split(double x) {
   const float hi = __double2float_rn(x);

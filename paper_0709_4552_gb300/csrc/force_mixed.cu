@@ -59,15 +59,6 @@ __global__ void __launch_bounds__(NT) force_mixed_fused_kernel(
                              finalize != 0, tbox, ord, 0, fa, nbk::ISrc(), true);
 }
 
-// (hi, lo) += (bh, bl): double-single sum (Knuth's TwoSum of the high parts,
-// the low parts and the rounding error added without renormalisation)
-__device__ __forceinline__ void ds_acc(float& hi, float& lo, float bh, float bl) {
-  const float s = hi + bh;
-  const float bb = s - hi;
-  lo = (lo + bl) + ((hi - (s - bb)) + (bh - bb));
-  hi = s;
-}
-
 // Split-j reduction of double-single partials: CTA (32 x kQL threads) =
 // 32 consecutive list positions (coalesced rows) x kQL lanes over the
 // splits; lane ty sums splits ty, ty + kQL, ... in order (loads in batches of
@@ -94,11 +85,11 @@ __global__ void __launch_bounds__(32 * kQL) split_reduce_ds_kernel(const float2*
 #pragma unroll
         for (int b = 0; b < kB; ++b) v[b] = src[(int64_t)q * 7 * stride + b * step];
 #pragma unroll
-        for (int b = 0; b < kB; ++b) ds_acc(hi, lo, v[b].x, v[b].y);
+        for (int b = 0; b < kB; ++b) nbk::ds_add(hi, lo, v[b].x, v[b].y);
       }
       for (; q < nsplit; q += kQL) {
         const float2 v = src[(int64_t)q * 7 * stride];
-        ds_acc(hi, lo, v.x, v.y);
+        nbk::ds_add(hi, lo, v.x, v.y);
       }
     }
     sm[ty][tx] = make_float2(hi, lo);
@@ -108,7 +99,7 @@ __global__ void __launch_bounds__(32 * kQL) split_reduce_ds_kernel(const float2*
       if (ty < h) {
         float2 a = sm[ty][tx];
         const float2 b = sm[ty + h][tx];
-        ds_acc(a.x, a.y, b.x, b.y);
+        nbk::ds_add(a.x, a.y, b.x, b.y);
         sm[ty][tx] = a;
       }
       __syncthreads();

@@ -39,6 +39,157 @@ __device__ __forceinline__ double clamp_dt(double c, double dt_min, double dt_ma
   return c;
 }
 
+// ---- exact integer forms of FP64 operations with exact results -------------
+// On this GPU a warp's FP64 instruction occupies it for about 64 cycles, and
+// the corrector's chain is the critical path of a small block step.  Where an
+// FP64 operation's result is exact -- a power of two raised to a power, a
+// constant scaled by a power of two, the power-of-two floor of a correctly
+// rounded square root, comparisons -- it is formed from the exponent bits
+// instead: the same bits, no FP64 instruction.  Outside the stated
+// preconditions the FP64 expression is taken.
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// x a positive normal power of two: its exponent in e
+__device__ __forceinline__ bool is_pow2(double x, int& e) {
+  const unsigned long long b = dbits(x);
+  const unsigned long long E = b >> 52;  // sign bit 0 and biased exponent
+  e = (int)E - 1023;
+  return (b & 0x000FFFFFFFFFFFFFULL) == 0 && E >= 1 && E <= 2046;
+}
+
+// 2^e, e in [-1022, 1023]
+__device__ __forceinline__ double pow2i(int e) {
+  return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
+}
+
+// c 2^k for a positive normal c whose scaled exponent stays normal (the
+// callers' ranges guarantee it): exact, so equal to the FP64 product
+__device__ __forceinline__ double scale_pow2(double c, int k) {
+  return __longlong_as_double((long long)(dbits(c) + ((unsigned long long)(long long)k << 52)));
+}
+
+// powers of the step h = t - t_i and the constant multiples the corrector
+// uses: from the exponent when h is a power of two 2^e with |e| <= 200 (every
+// block step; all results normal), else by FP64 products
+struct HPow {
+  double ih, ih2, ih3, h2, h3, h4, h5;
+  double h3_6, h4_24, h5_120, h6;  // h^3/6, h^4/24, h^5/120, 6h
+};
+// the FP64 products (the reference of the exponent form, and its fallback)
+__device__ __forceinline__ HPow h_powers_fp64(double h) {
+  HPow q;
+  q.ih = div_pow2(1.0, h);
+  q.ih2 = q.ih * q.ih;
+  q.ih3 = q.ih2 * q.ih;
+  q.h2 = h * h;
+  q.h3 = q.h2 * h;
+  q.h4 = q.h3 * h;
+  q.h5 = q.h4 * h;
+  q.h3_6 = q.h3 * (1.0 / 6.0);
+  q.h4_24 = q.h4 * (1.0 / 24.0);
+  q.h5_120 = q.h5 * (1.0 / 120.0);
+  q.h6 = 6.0 * h;
+  return q;
+}
+
+__device__ __forceinline__ HPow h_powers(double h) {
+  HPow q;
+  int e;
+  if (is_pow2(h, e) && e >= -200 && e <= 200) {
+    q.ih = pow2i(-e);
+    q.ih2 = pow2i(-2 * e);
+    q.ih3 = pow2i(-3 * e);
+    q.h2 = pow2i(2 * e);
+    q.h3 = pow2i(3 * e);
+    q.h4 = pow2i(4 * e);
+    q.h5 = pow2i(5 * e);
+    q.h3_6 = scale_pow2(1.0 / 6.0, 3 * e);
+    q.h4_24 = scale_pow2(1.0 / 24.0, 4 * e);
+    q.h5_120 = scale_pow2(1.0 / 120.0, 5 * e);
+    q.h6 = scale_pow2(6.0, e);
+    return q;
+  }
+  return h_powers_fp64(h);
+}
+
+// t (>= 0) an integer multiple of 2^s: 1 yes, 0 no, -1 undecided here
+// (negative, subnormal or non-finite t, or t 2^-s below the normal range)
+__device__ __forceinline__ int multiple_of_pow2(double t, int s) {
+  const unsigned long long b = dbits(t);
+  if (b == 0) return 1;
+  const unsigned long long E = b >> 52;
+  if (E == 0 || E >= 2047) return -1;
+  const int d = (int)E - 1023 - s;  // t 2^-s = 1.f 2^d
+  if (d < -1000) return -1;
+  if (d < 0) return 0;
+  if (d >= 52) return 1;
+  return (b & ((1ULL << (52 - d)) - 1ULL)) == 0 ? 1 : 0;
+}
+
+// The new step (Sec. 4.1 step 5; block steps of Sec. 2) of a particle at time
+// t with step dt_old, from num = na n2 + nj^2 and den = nj n3 + n2^2 (na =
+// |a1|, nj = |j1|, n2 = |a2 + a3 h|, n3 = |a3|): Aarseth criterion
+// crit = sqrt(eta num / den), its power-of-two floor clamped to [dt_min,
+// dt_max]; the step shrinks to that freely and doubles only when t is a
+// multiple of the doubled step (and the doubled step is admissible).  Counts
+// criteria below dt_min; crit_nan reports a NaN criterion.  This is the FP64
+// expression: the reference of new_step_nd's exponent form and its fallback.
+__device__ __forceinline__ double new_step_fp64(double t, double dt_old, double num, double den, double eta,
+                                                double dt_min, double dt_max, nb_dev_status* st, bool& crit_nan) {
+  const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
+  if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
+  crit_nan = isnan(crit);
+  const double c = clamp_dt(pow2_floor(crit), dt_min, dt_max);
+  if (c < dt_old) return c;
+  const double two = 2.0 * dt_old;
+  const double qq = div_pow2(t, two);  // exact: two is a power of two
+  return (c >= two && two <= dt_max && qq == floor(qq)) ? two : dt_old;
+}
+
+// new_step_fp64's result from exponents.  For positive normal N = fl(eta num)
+// and D = den, fl(N / D) has exponent e_N - e_D, less one when N's
+// significand is below D's (a quotient of 53-bit significands never rounds up
+// to a power of two), and the power-of-two floor of the correctly rounded
+// square root of q = fl(N / D) is 2^floor(e_q / 2) (the square root never
+// rounds up to a power of two either); crit < dt_min = 2^m exactly when
+// e_q < 2m.  So no division or square root is needed; they are taken (the
+// FP64 expression) only when an operand is zero, subnormal or non-finite, a
+// step bound or dt_old is not a power of two, or t is negative or subnormal.
+__device__ __forceinline__ double new_step_nd(double t, double dt_old, double num, double den, double eta,
+                                              double dt_min, double dt_max, nb_dev_status* st, bool& crit_nan) {
+  crit_nan = false;
+  int emin, emax, eo;
+  if (den != 0.0 && is_pow2(dt_min, emin) && is_pow2(dt_max, emax) && is_pow2(dt_old, eo) && emin <= emax) {
+    const double nq = eta * num;
+    const unsigned long long bN = dbits(nq), bD = dbits(den);
+    const unsigned long long EN = bN >> 52, ED = bD >> 52;  // sign bits 0 for positive operands
+    if (EN >= 1 && EN <= 2046 && ED >= 1 && ED <= 2046) {
+      const int eq = (int)EN - (int)ED - ((bN & 0x000FFFFFFFFFFFFFULL) < (bD & 0x000FFFFFFFFFFFFFULL) ? 1 : 0);
+      const int s = eo + 1;  // the doubled step 2^s
+      const int mt = eq >= -1022 && eq <= 1023 ? multiple_of_pow2(t, s) : -1;
+      if (mt >= 0) {
+        if (eq < 2 * emin) atomicAdd(&st->dt_underflows, 1ULL);  // crit < dt_min
+        int ec = (eq - (eq & 1)) / 2;  // floor(eq / 2): exponent of the criterion's floor
+        if (ec > emax) ec = emax;
+        if (ec < emin) ec = emin;
+        if (ec < eo) return pow2i(ec);
+        return (ec >= s && s <= emax && mt == 1) ? pow2i(s) : dt_old;
+      }
+    }
+  }
+  return new_step_fp64(t, dt_old, num, den, eta, dt_min, dt_max, st, crit_nan);
+}
+
+// the step from the four norms' roots
+__device__ __forceinline__ double new_step(double t, double dt_old, double na, double nj, double n2, double n3,
+                                           double eta, double dt_min, double dt_max, nb_dev_status* st,
+                                           bool& crit_nan) {
+  const double num = na * n2 + nj * nj;
+  const double den = nj * n3 + n2 * n2;
+  return new_step_nd(t, dt_old, num, den, eta, dt_min, dt_max, st, crit_nan);
+}
+
 // Predictor (Sec. 4.1 step 3) of row i over h = t - t_i, Horner form:
 //   xp = x + v h + a h^2/2 + jk h^3/6,   vp = v + a h + jk h^2/2
 __device__ __forceinline__ void taylor(int64_t i, int64_t n_pad, double h, const double* __restrict__ x,
@@ -97,9 +248,7 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
                                             const double* __restrict__ xp, const double* __restrict__ vp,
                                             nb_dev_status* __restrict__ st) {
   const double h = t - ti[i];
-  const double ih = div_pow2(1.0, h);
-  const double ih2 = ih * ih, ih3 = ih2 * ih;
-  const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+  const HPow hp = h_powers(h);
   double na2 = 0, nj2 = 0, n22 = 0, n32 = 0;
   bool finite = true;
 #pragma unroll
@@ -108,10 +257,10 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
     const double a0 = a[q], j0 = jk[q];
     const double a1 = f[c], j1 = f[3 + c];
     const double da = a0 - a1;
-    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
-    const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
-    const double x1 = xp[q] + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
-    const double v1 = vp[q] + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * hp.ih2;
+    const double a3 = (12.0 * da + hp.h6 * (j0 + j1)) * hp.ih3;
+    const double x1 = xp[q] + a2 * hp.h4_24 + a3 * hp.h5_120;
+    const double v1 = vp[q] + a2 * hp.h3_6 + a3 * hp.h4_24;
     const double a2e = a2 + a3 * h;
     x[q] = x1;
     v[q] = v1;
@@ -126,21 +275,9 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
   const double p1 = f[6];
   pot[i] = p1;
   const double na = sqrt(na2), nj = sqrt(nj2), n2 = sqrt(n22), n3 = sqrt(n32);
-  const double num = na * n2 + nj * nj;
-  const double den = nj * n3 + n2 * n2;
-  const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
-  if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
-  const double dt_old = dt[i];
-  const double c = clamp_dt(pow2_floor(crit), dt_min, dt_max);
-  double dnew;
-  if (c < dt_old) {
-    dnew = c;
-  } else {
-    const double two = 2.0 * dt_old;
-    const double q = div_pow2(t, two);  // exact: two is a power of two
-    dnew = (c >= two && two <= dt_max && q == floor(q)) ? two : dt_old;
-  }
-  if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
+  bool crit_nan;
+  const double dnew = new_step(t, dt[i], na, nj, n2, n3, eta, dt_min, dt_max, st, crit_nan);
+  if (!finite || !isfinite(p1) || crit_nan) atomicOr(&st->flags, NB_ST_NUMERIC);
   ti[i] = t;
   dt[i] = dnew;
   return t + dnew;
@@ -178,9 +315,7 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
                                                  double* __restrict__ dt, nb_dev_status* __restrict__ st, int sub,
                                                  int base, bool write, float4* __restrict__ jm = nullptr) {
   const double h = t - in.t0;
-  const double ih = div_pow2(1.0, h);
-  const double ih2 = ih * ih, ih3 = ih2 * ih;
-  const double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+  const HPow hp = h_powers(h);
   double sq[4] = {0.0, 0.0, 0.0, 0.0};  // a1^2, j1^2, a2e^2, a3^2 of this lane's component
   double ab[3];                         // |v1|, |a1|, |j1| of this lane's component (the record's reach)
   int fin = 1;
@@ -192,10 +327,10 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
     const double a1 = c == 0 ? f[0] : (c == 1 ? f[1] : f[2]);
     const double j1 = c == 0 ? f[3] : (c == 1 ? f[4] : f[5]);
     const double da = a0 - a1;
-    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * ih2;
-    const double a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * ih3;
-    const double x1 = in.xp + a2 * (h4 * (1.0 / 24.0)) + a3 * (h5 * (1.0 / 120.0));
-    const double v1 = in.vp + a2 * (h3 * (1.0 / 6.0)) + a3 * (h4 * (1.0 / 24.0));
+    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * hp.ih2;
+    const double a3 = (12.0 * da + hp.h6 * (j0 + j1)) * hp.ih3;
+    const double x1 = in.xp + a2 * hp.h4_24 + a3 * hp.h5_120;
+    const double v1 = in.vp + a2 * hp.h3_6 + a3 * hp.h4_24;
     const double a2e = a2 + a3 * h;
     if (write && sub < 3) {
       x[q] = x1;
@@ -255,22 +390,10 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
   if (!write || sub != 0) return 0.0;
   const double p1 = f[6];
   pot[i] = p1;
-  const double num = na * n2 + nj * nj;
-  const double den = nj * n3 + n2 * n2;
-  const double crit = (den == 0.0) ? (double)INFINITY : sqrt(eta * num / den);
-  if (crit < dt_min) atomicAdd(&st->dt_underflows, 1ULL);
-  const double dt_old = in.dt0;
-  const double cl = clamp_dt(pow2_floor(crit), dt_min, dt_max);
-  double dnew;
-  if (cl < dt_old) {
-    dnew = cl;
-  } else {
-    const double two = 2.0 * dt_old;
-    const double qq = div_pow2(t, two);  // exact: two is a power of two
-    dnew = (cl >= two && two <= dt_max && qq == floor(qq)) ? two : dt_old;
-  }
+  bool crit_nan;
+  const double dnew = new_step(t, in.dt0, na, nj, n2, n3, eta, dt_min, dt_max, st, crit_nan);
   const bool finite = f0 && f1 && f2;
-  if (!finite || !isfinite(p1) || isnan(crit)) atomicOr(&st->flags, NB_ST_NUMERIC);
+  if (!finite || !isfinite(p1) || crit_nan) atomicOr(&st->flags, NB_ST_NUMERIC);
   ti[i] = t;
   dt[i] = dnew;
   if (jm) {

@@ -350,6 +350,7 @@ __device__ __forceinline__ int64_t loop_splits(int64_t n, int64_t jtiles, unsign
 // of this CTA's own list positions [before, before + mycnt).  The step's
 // values are read from shared memory here rather than kept in registers
 // across the force items.
+template <bool MIXED>
 __device__ void correct_own(const LoopArgs& p, LoopSmem& s, int64_t jtiles, unsigned int G, int64_t r0,
                             int64_t r1) {
   const long long before = s.before;
@@ -380,6 +381,31 @@ __device__ void correct_own(const LoopArgs& p, LoopSmem& s, int64_t jtiles, unsi
       if (have && l < 4)
 #pragma unroll
         for (int r = 0; r < 7; ++r) f[r] = p.F[r * p.n_pad + k];
+    } else if (MIXED) {
+      // double-single partials (the mixed item's split output): summed and
+      // exchanged in FP32 (a warp's FP64 instruction costs it 64 cycles
+      // here), converted to FP64 once
+      float hi[7], lo[7];
+#pragma unroll
+      for (int r = 0; r < 7; ++r) hi[r] = lo[r] = 0.0f;
+      const float2* part2 = reinterpret_cast<const float2*>(p.part);
+      if (have)
+        for (int64_t sp = l; sp < S; sp += L)
+#pragma unroll
+          for (int r = 0; r < 7; ++r) {
+            const float2 v = part2[(sp * 7 + r) * pstride + k];
+            nbk::ds_add(hi[r], lo[r], v.x, v.y);
+          }
+      for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < 7; ++r) {
+          const float oh = __shfl_xor_sync(0xffffffffu, hi[r], o);
+          const float ol = __shfl_xor_sync(0xffffffffu, lo[r], o);
+          nbk::ds_add(hi[r], lo[r], oh, ol);
+        }
+#pragma unroll
+      for (int r = 0; r < 7; ++r) f[r] = (double)hi[r] + (double)lo[r];
+      f[6] = -f[6];
     } else {
 #pragma unroll
       for (int r = 0; r < 7; ++r) f[r] = 0.0;
@@ -498,13 +524,13 @@ __global__ void __launch_bounds__(kLT, kLMaxPerSm) loop_kernel(LoopArgs p) {
       const int64_t ostride = fin ? p.n_pad : pstride;
       if constexpr (MIXED)
         nbk::mixed_item<kLT, 1, kLMixJT>(fsm, p.jA, p.jB, p.jC, jlo, jhi, n_j, p.act, n, itile * kLT, p.eps2f,
-                                         out, ostride, fin, p.tbox, nullptr, 0);
+                                         out, ostride, fin, p.tbox, nullptr, 0, nbk::FusedArgs(), nbk::ISrc(), true);
       else
         nbk::fp64_item<kLT, kLF64JT>(fsm, p.xp, p.vp, p.m, p.n_pad, jlo, jhi, p.act, n, itile * kLT, p.eps2, out,
                                      ostride, fin);
     }
     if (!grid_barrier(p.ctl, epoch, G, p.st, &s.ok)) return;  // C: forces complete
-    correct_own(p, s, jtiles, G, r0, r1);
+    correct_own<MIXED>(p, s, jtiles, G, r0, r1);
     ++steps;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       p.ctl->steps = steps;

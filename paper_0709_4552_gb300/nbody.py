@@ -39,7 +39,7 @@ EXPORTS = (
     "nb_get_predicted", "nb_forces_on", "nb_set_forces", "nb_set_initial_forces", "nb_set_jpredict", "nb_get_jpredict", "nb_correct", "nb_initial_forces_and_dt", "nb_step", "nb_integrate",
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
-    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_autotune", "nb_autotune_list", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
+    "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_selftest_corrector", "nb_autotune", "nb_autotune_list", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
     "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
@@ -110,6 +110,7 @@ def lib():
         "nb_set_tuning": (_int, [_vp, _int, _int, _int, _int]),
         "nb_set_far_tiles": (_int, [_vp, _int]),
         "nb_get_far_tiles": (_int, [_vp, _pint]),
+        "nb_selftest_corrector": (_int, [_int, _i64, ctypes.c_uint64, ctypes.POINTER(_i64)]),
         "nb_autotune": (_int, [_vp, _i64, _pint, _pint, _pint, _pint]),
         "nb_autotune_list": (_int, [_vp, _vp, _i64, _int, _pint, _pint, _pint, _pint]),
         "nb_ensemble_autotune": (_int, [_vp, _i64, _pint, _pint, _pd, _pd]),
@@ -463,6 +464,15 @@ def nb_autotune(ctx, n):
     v = [_int() for _ in range(4)]
     _check(lib().nb_autotune(ctx, int(n), *[ctypes.byref(x) for x in v]), "nb_autotune")
     return dict(i_per_thread=v[0].value, threads=v[1].value, j_tile=v[2].value, n_split=v[3].value)
+
+
+def nb_selftest_corrector(samples=1 << 20, seed=1, device=0):
+    """Mismatches of the corrector's exponent forms against their FP64
+    expressions on `samples` random operand sets (0 expected)."""
+    out = _i64()
+    _check(lib().nb_selftest_corrector(int(device), int(samples), int(seed), ctypes.byref(out)),
+           "nb_selftest_corrector")
+    return int(out.value)
 
 
 def nb_autotune_list(ctx, i_idx):

@@ -418,3 +418,11 @@ def test_resident_order_random_api_sequence(nbl):
                 sub = s.get_particles(lo, cnt)
                 for k in ("m", "x", "v", "a", "jerk", "t", "dt"):
                     assert np.array_equal(sub[k], st[k][lo:lo + cnt]), k
+
+
+def test_corrector_exponent_forms_bitwise(nbl):
+    # the corrector's shortcuts (powers of a power-of-two step, the step rule
+    # from exponents) give their FP64 expressions' bits on 4M random operand
+    # sets, boundary and non-finite cases included
+    assert nbl.nb_selftest_corrector(1 << 22, seed=11) == 0
+    assert nbl.nb_selftest_corrector(1 << 20, seed=12) == 0
