@@ -830,6 +830,9 @@ def main():
         extra["fp64_gpu_path"] = {"value": fp64_rate, "unit": UNIT,
                                   "sample": f"{k} active x N={N}", "vs_mixed": fp64_rate / value * ws,
                                   "fp64_pipe_frac": fp64_rate * 32 / (pk["fp64_tflops"] * 1e12 / 2)}
+        # how the FP64 unit issues (cycles per FMA for one warp, dependent chain with 32 or 1
+        # lanes, four chains; SM cycles per warp instruction with 16 warps)
+        pk["fp64_issue_cycles"] = s.measure_fp64_issue()
         extra["peaks_measured"] = pk
         if not args.no_cpu and ws == 1:  # the host baseline is taken at N = 1 only
             import oracle

@@ -492,6 +492,19 @@ int nb_tune_clear(nb_ctx* ctx);
  */
 int nb_measure_peaks(nb_ctx* ctx, double* fp32_tflops, double* fp64_tflops, double* rsqrt_tops);
 
+/*
+ * nb_measure_fp64_issue -- how the context's GPU issues FP64 instructions, in
+ * SM cycles per FP64 FMA (clock64 around chains of 4096 FMAs in one CTA):
+ * *dep32 one warp, all 32 lanes, a dependent chain; *dep1 the same with one
+ * lane active; *indep4 one warp, four independent chains (per instruction);
+ * *sm16 sixteen warps on one SM, SM cycles per warp instruction.  On GB300
+ * each is ~64, ~64, ~64 and ~19: a warp issues one FP64 instruction per ~64
+ * cycles whatever its active lanes, which is why the small-block paths keep
+ * FP64 off their critical paths (not in the paper).  Uses the context's
+ * scratch; any pointer may be NULL.  Errors: NB_EINVAL, NB_ECUDA.
+ */
+int nb_measure_fp64_issue(nb_ctx* ctx, double* dep32, double* dep1, double* indep4, double* sm16);
+
 /* ---- batched ensemble of independent clusters --------------------------- */
 /*
  * nb_ensemble_create -- a context for n_clusters independent systems stored

@@ -286,6 +286,12 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       s.jzh[q] = hi; s.jzl[q] = lo; s.jvz[q] = vv;
       s.jms[q] = R0.w;
     }
+    if ((nr & 1) && tid == kCT - 1) {  // the pair loop's padding row: massless, far away
+      s.jxh[nr] = s.jyh[nr] = s.jzh[nr] = nbk::kFarF;
+      s.jxl[nr] = s.jyl[nr] = s.jzl[nr] = 0.0f;
+      s.jvx[nr] = s.jvy[nr] = s.jvz[nr] = 0.0f;
+      s.jms[nr] = 0.0f;
+    }
     __syncthreads();
     // push this CTA's particles of the first group into every CTA's group
     // buffer (every CTA finished reading its buffer before barrier A)
@@ -334,35 +340,54 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
         const float xh = A.x, yh = A.y, zh = A.z, xl = B.x, yl = B.y, zl = B.z;
         const float vx = A.w, vy = B.w, vz = Ci.x;
         const int self = own_index(__float_as_int(Ci.y), me, C);  // -1: held by another CTA
-        const int q0 = (int)((int64_t)part * nr / P), q1 = (int)((int64_t)(part + 1) * nr / P);
-        for (int c0 = q0; c0 < q1; c0 += kChunk) {
-          const int c1 = min(c0 + kChunk, q1);
-          float pp[7];
+        // pairs of own rows (2u, 2u + 1) in packed FP32x2 instructions (two j per
+        // instruction, as the force item's pair loop); an odd row count ends in
+        // the massless far-away padding row nr
+        const int np = (nr + 1) / 2;
+        const int u0 = (int)((int64_t)part * np / P), u1 = (int)((int64_t)(part + 1) * np / P);
+        const float2 nxh = make_float2(-xh, -xh), nyh = make_float2(-yh, -yh), nzh = make_float2(-zh, -zh);
+        const float2 nxl = make_float2(-xl, -xl), nyl = make_float2(-yl, -yl), nzl = make_float2(-zl, -zl);
+        const float2 nvx = make_float2(-vx, -vx), nvy = make_float2(-vy, -vy), nvz = make_float2(-vz, -vz);
+        const float2 e2 = make_float2(p.eps2f, p.eps2f), m3 = make_float2(-3.0f, -3.0f);
+        const float2* JXH = reinterpret_cast<const float2*>(s.jxh);
+        const float2* JYH = reinterpret_cast<const float2*>(s.jyh);
+        const float2* JZH = reinterpret_cast<const float2*>(s.jzh);
+        const float2* JXL = reinterpret_cast<const float2*>(s.jxl);
+        const float2* JYL = reinterpret_cast<const float2*>(s.jyl);
+        const float2* JZL = reinterpret_cast<const float2*>(s.jzl);
+        const float2* JVX = reinterpret_cast<const float2*>(s.jvx);
+        const float2* JVY = reinterpret_cast<const float2*>(s.jvy);
+        const float2* JVZ = reinterpret_cast<const float2*>(s.jvz);
+        const float2* JMS = reinterpret_cast<const float2*>(s.jms);
+        for (int c0 = u0; c0 < u1; c0 += kChunk / 2) {
+          const int c1 = min(c0 + kChunk / 2, u1);
+          float2 pp[7];
 #pragma unroll
-          for (int c = 0; c < 7; ++c) pp[c] = 0.0f;
-          for (int q = c0; q < c1; ++q) {
-            const float dx = (s.jxh[q] - xh) + (s.jxl[q] - xl);
-            const float dy = (s.jyh[q] - yh) + (s.jyl[q] - yl);
-            const float dz = (s.jzh[q] - zh) + (s.jzl[q] - zl);
-            const float wx = s.jvx[q] - vx, wy = s.jvy[q] - vy, wz = s.jvz[q] - vz;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, p.eps2f)));
-            const float rw = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
-            float rinv = nb_rsqrt_approx(r2);
-            rinv = (q == self) ? 0.0f : rinv;  // the self pair, by row
-            const float rinv2 = rinv * rinv;
-            const float mr = s.jms[q] * rinv;
-            const float mr3 = mr * rinv2;
-            const float a3 = (rw * -3.0f) * rinv2;  // the jerk term formed before it is added
-            pp[6] += mr;
-            pp[0] = fmaf(mr3, dx, pp[0]);
-            pp[1] = fmaf(mr3, dy, pp[1]);
-            pp[2] = fmaf(mr3, dz, pp[2]);
-            pp[3] = fmaf(mr3, fmaf(a3, dx, wx), pp[3]);
-            pp[4] = fmaf(mr3, fmaf(a3, dy, wy), pp[4]);
-            pp[5] = fmaf(mr3, fmaf(a3, dz, wz), pp[5]);
+          for (int c = 0; c < 7; ++c) pp[c] = make_float2(0.0f, 0.0f);
+          for (int u = c0; u < c1; ++u) {
+            const float2 dx = __fadd2_rn(__fadd2_rn(JXH[u], nxh), __fadd2_rn(JXL[u], nxl));
+            const float2 dy = __fadd2_rn(__fadd2_rn(JYH[u], nyh), __fadd2_rn(JYL[u], nyl));
+            const float2 dz = __fadd2_rn(__fadd2_rn(JZH[u], nzh), __fadd2_rn(JZL[u], nzl));
+            const float2 wx = __fadd2_rn(JVX[u], nvx), wy = __fadd2_rn(JVY[u], nvy), wz = __fadd2_rn(JVZ[u], nvz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
+            const float2 rw = __ffma2_rn(dz, wz, __ffma2_rn(dy, wy, __fmul2_rn(dx, wx)));
+            float2 rinv = make_float2(nb_rsqrt_approx(r2.x), nb_rsqrt_approx(r2.y));
+            rinv.x = (2 * u == self) ? 0.0f : rinv.x;  // the self pair, by row
+            rinv.y = (2 * u + 1 == self) ? 0.0f : rinv.y;
+            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+            const float2 mr = __fmul2_rn(JMS[u], rinv);
+            const float2 mr3 = __fmul2_rn(mr, rinv2);
+            const float2 a3 = __fmul2_rn(__fmul2_rn(rw, m3), rinv2);  // the jerk term formed before it is added
+            pp[6] = __fadd2_rn(pp[6], mr);
+            pp[0] = __ffma2_rn(mr3, dx, pp[0]);
+            pp[1] = __ffma2_rn(mr3, dy, pp[1]);
+            pp[2] = __ffma2_rn(mr3, dz, pp[2]);
+            pp[3] = __ffma2_rn(mr3, __ffma2_rn(a3, dx, wx), pp[3]);
+            pp[4] = __ffma2_rn(mr3, __ffma2_rn(a3, dy, wy), pp[4]);
+            pp[5] = __ffma2_rn(mr3, __ffma2_rn(a3, dz, wz), pp[5]);
           }
 #pragma unroll
-          for (int c = 0; c < 7; ++c) nbk::ds_add(hi7[c], lo7[c], pp[c], 0.0f);  // double-single fold
+          for (int c = 0; c < 7; ++c) nbk::ds_add(hi7[c], lo7[c], pp[c].x + pp[c].y, 0.0f);  // double-single fold
         }
       }
       // the P parts of a particle, lanes of one warp: a double-single

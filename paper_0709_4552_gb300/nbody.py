@@ -40,7 +40,7 @@ EXPORTS = (
     "nb_energy", "nb_get_timings", "nb_get_counters", "nb_check_device_status", "nb_check_grid_barrier",
     "nb_last_error", "nb_clear_error",
     "nb_set_tuning", "nb_set_far_tiles", "nb_get_far_tiles", "nb_selftest_corrector", "nb_autotune", "nb_autotune_list", "nb_ensemble_autotune", "nb_tune_save", "nb_tune_load", "nb_tune_count", "nb_tune_clear",
-    "nb_measure_peaks", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
+    "nb_measure_peaks", "nb_measure_fp64_issue", "nb_ensemble_create", "nb_ensemble_initial_forces_and_dt",
     "nb_ensemble_integrate", "nb_ensemble_energy", "nb_forces_fp64_noalloc", "nb_strerror", "nb_version",
 )
 
@@ -120,6 +120,7 @@ def lib():
         "nb_tune_clear": (_int, [_vp]),
         "nb_ensemble_create": (_int, [ctypes.POINTER(_vp), _i32, _vp, _vp, _int, _int, _vp]),
         "nb_measure_peaks": (_int, [_vp, _pd, _pd, _pd]),
+        "nb_measure_fp64_issue": (_int, [_vp, _pd, _pd, _pd, _pd]),
         "nb_ensemble_initial_forces_and_dt": (_int, [_vp]),
         "nb_ensemble_integrate": (_int, [_vp, _d, _int]),
         "nb_ensemble_energy": (_int, [_vp, _vp, _vp]),
@@ -516,6 +517,13 @@ def nb_measure_peaks(ctx):
     v = [_d() for _ in range(3)]
     _check(lib().nb_measure_peaks(ctx, *[ctypes.byref(x) for x in v]), "nb_measure_peaks")
     return dict(fp32_tflops=v[0].value, fp64_tflops=v[1].value, rsqrt_tops=v[2].value)
+
+
+def nb_measure_fp64_issue(ctx):
+    v = [_d() for _ in range(4)]
+    _check(lib().nb_measure_fp64_issue(ctx, *[ctypes.byref(x) for x in v]), "nb_measure_fp64_issue")
+    return dict(dep32_cycles=v[0].value, dep1_cycles=v[1].value, indep4_cycles=v[2].value,
+                sm16_cycles_per_warp_instr=v[3].value)
 
 
 def nb_ensemble_create(offsets, eps, precision=NB_MIXED, device=0, stream=None):

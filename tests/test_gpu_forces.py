@@ -229,3 +229,12 @@ def test_far_tiles_off_is_strict(nbl):
         ea, ej, ep = _check(nbl.NB_MIXED, nbl, got[far], ref)
         print(f"far tiles {far}: acc {np.median(ea):.2e}/{ea.max():.2e} jerk {np.median(ej):.2e}/{ej.max():.2e}")
     assert not np.array_equal(got[True][0], got[False][0])
+
+
+def test_fp64_issue_probe_runs(nbl):
+    # the FP64 issue probe returns positive cycle counts for every layout, and
+    # one warp is not faster with one lane than with 32 (a whole-warp cost)
+    with nbl.NBody(1024, nbl.NB_MIXED, 0) as s:
+        r = s.measure_fp64_issue()
+    assert all(np.isfinite(v) and v > 0 for v in r.values())
+    assert r["dep1_cycles"] >= 0.9 * r["dep32_cycles"]
