@@ -75,7 +75,28 @@ __device__ __forceinline__ double scale_pow2(double c, int k) {
 struct HPow {
   double ih, ih2, ih3, h2, h3, h4, h5;
   double h3_6, h4_24, h5_120, h6;  // h^3/6, h^4/24, h^5/120, 6h
+  int e;                           // h = 2^e when pow2
+  bool pow2;
 };
+
+// y 2^k, exact: from the exponent bits when y is finite and normal and the
+// result stays normal, else the FP64 product y p2 with p2 = 2^k (the same
+// value; infinities and NaNs take the product)
+__device__ __forceinline__ double mul_pow2(double y, int k, double p2) {
+  const unsigned long long b = dbits(y);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E >= 1 && E <= 2046 && E + k >= 1 && E + k <= 2046)  // y finite and normal, so is the result
+    return __longlong_as_double((long long)(b + ((unsigned long long)(long long)k << 52)));
+  return y * p2;
+}
+
+// y / h^2 and y / h^3 of the corrector (products by the exact inverse powers)
+__device__ __forceinline__ double div_h2(const struct HPow& q, double y) {
+  return q.pow2 ? mul_pow2(y, -2 * q.e, q.ih2) : y * q.ih2;
+}
+__device__ __forceinline__ double div_h3(const struct HPow& q, double y) {
+  return q.pow2 ? mul_pow2(y, -3 * q.e, q.ih3) : y * q.ih3;
+}
 // the FP64 products (the reference of the exponent form, and its fallback)
 __device__ __forceinline__ HPow h_powers_fp64(double h) {
   HPow q;
@@ -90,6 +111,8 @@ __device__ __forceinline__ HPow h_powers_fp64(double h) {
   q.h4_24 = q.h4 * (1.0 / 24.0);
   q.h5_120 = q.h5 * (1.0 / 120.0);
   q.h6 = 6.0 * h;
+  q.e = 0;
+  q.pow2 = false;
   return q;
 }
 
@@ -97,6 +120,8 @@ __device__ __forceinline__ HPow h_powers(double h) {
   HPow q;
   int e;
   if (is_pow2(h, e) && e >= -200 && e <= 200) {
+    q.e = e;
+    q.pow2 = true;
     q.ih = pow2i(-e);
     q.ih2 = pow2i(-2 * e);
     q.ih3 = pow2i(-3 * e);
@@ -257,8 +282,8 @@ __device__ __forceinline__ double correct_row(int64_t i, int64_t n_pad, double t
     const double a0 = a[q], j0 = jk[q];
     const double a1 = f[c], j1 = f[3 + c];
     const double da = a0 - a1;
-    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * hp.ih2;
-    const double a3 = (12.0 * da + hp.h6 * (j0 + j1)) * hp.ih3;
+    const double a2 = div_h2(hp, -6.0 * da - h * (4.0 * j0 + 2.0 * j1));
+    const double a3 = div_h3(hp, 12.0 * da + hp.h6 * (j0 + j1));
     const double x1 = xp[q] + a2 * hp.h4_24 + a3 * hp.h5_120;
     const double v1 = vp[q] + a2 * hp.h3_6 + a3 * hp.h4_24;
     const double a2e = a2 + a3 * h;
@@ -327,8 +352,8 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
     const double a1 = c == 0 ? f[0] : (c == 1 ? f[1] : f[2]);
     const double j1 = c == 0 ? f[3] : (c == 1 ? f[4] : f[5]);
     const double da = a0 - a1;
-    const double a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * hp.ih2;
-    const double a3 = (12.0 * da + hp.h6 * (j0 + j1)) * hp.ih3;
+    const double a2 = div_h2(hp, -6.0 * da - h * (4.0 * j0 + 2.0 * j1));
+    const double a3 = div_h3(hp, 12.0 * da + hp.h6 * (j0 + j1));
     const double x1 = in.xp + a2 * hp.h4_24 + a3 * hp.h5_120;
     const double v1 = in.vp + a2 * hp.h3_6 + a3 * hp.h4_24;
     const double a2e = a2 + a3 * h;
@@ -357,16 +382,19 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
     ab[2] = fabs(j1);
     fin = (isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1)) ? 1 : 0;
   }
-  // norms summed in component order on every lane (0 + x^2 + y^2 + z^2, as
-  // correct_row's running sums); every shuffle is taken by every lane
-  double nrm2[4];
+  // lane sub (< 4) sums squared norm `sub` in component order (0 + x^2 +
+  // y^2 + z^2, as correct_row's running sums): three FP64 adds per lane
+  // instead of all four norms on every lane; every shuffle is taken by every lane
+  double own[3];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const double s0 = __shfl_sync(0xffffffffu, sq[r], base);
-    const double s1 = __shfl_sync(0xffffffffu, sq[r], base + 1);
-    const double s2 = __shfl_sync(0xffffffffu, sq[r], base + 2);
-    nrm2[r] = ((0.0 + s0) + s1) + s2;
+  for (int k = 0; k < 3; ++k) {
+    const double t0 = __shfl_sync(0xffffffffu, sq[0], base + k);
+    const double t1 = __shfl_sync(0xffffffffu, sq[1], base + k);
+    const double t2 = __shfl_sync(0xffffffffu, sq[2], base + k);
+    const double t3 = __shfl_sync(0xffffffffu, sq[3], base + k);
+    own[k] = sub == 1 ? t1 : (sub == 2 ? t2 : (sub == 3 ? t3 : t0));
   }
+  const double mine = ((0.0 + own[0]) + own[1]) + own[2];
   double sum_ab[3] = {0.0, 0.0, 0.0};  // write_jm_record's sums of |v|, |a|, |j| in component order
   if (jm) {
 #pragma unroll
@@ -381,7 +409,6 @@ __device__ __forceinline__ double correct_lanes4(int64_t i, int64_t n_pad, doubl
   const int f1 = __shfl_sync(0xffffffffu, fin, base + 1);
   const int f2 = __shfl_sync(0xffffffffu, fin, base + 2);
   // one square root per lane, gathered on lane 0
-  const double mine = sub == 1 ? nrm2[1] : (sub == 2 ? nrm2[2] : (sub == 3 ? nrm2[3] : nrm2[0]));
   const double root = sqrt(mine);
   const double na = __shfl_sync(0xffffffffu, root, base);
   const double nj = __shfl_sync(0xffffffffu, root, base + 1);

@@ -1,6 +1,7 @@
 // selftest.cu -- device self-check of the corrector's exponent forms
-// (hermite.cuh: h_powers, new_step_nd) against their FP64 expressions
-// (h_powers_fp64, new_step_fp64) on seeded random operands, bit for bit.
+// (hermite.cuh: h_powers, mul_pow2, new_step_nd) against their FP64
+// expressions (h_powers_fp64, the product by 2^k, new_step_fp64) on seeded
+// random operands, bit for bit.
 // The operands cover the block-step regime and its edges: powers of two and
 // other steps, significands of N = eta num and den equal or one unit apart
 // (quotients at a power-of-two boundary), zero, subnormal, infinite and NaN
@@ -56,6 +57,15 @@ __global__ void selftest_kernel(int64_t samples, uint64_t seed, unsigned long lo
       const double* pb = &b.ih;
       for (int q = 0; q < 11; ++q)
         if (nbh::dbits(pa[q]) != nbh::dbits(pb[q])) atomicAdd(bad, 1ULL);
+    }
+    // exact power-of-two scaling: y 2^k from the exponent bits against the
+    // FP64 product (y normal, subnormal, zero, infinite or NaN; results that
+    // stay normal, leave the normal range or overflow)
+    {
+      const int k = -600 + (int)((r2 >> 20) % 1201);
+      const double y = (r3 & 3) == 0 ? random_norm(r4, r5) : make_pos(1 + (int)((r4 >> 8) % 2046), r5);
+      const double ys = (r1 >> 63) ? -y : y;
+      if (nbh::dbits(nbh::mul_pow2(ys, k, nbh::pow2i(k))) != nbh::dbits(ys * nbh::pow2i(k))) atomicAdd(bad, 1ULL);
     }
     // the step rule
     const int emin = -30 + (int)(r0 >> 40) % 12;           // dt_min = 2^emin
