@@ -527,11 +527,12 @@ def run_integration(args):
         # n = 0.20 N^0.81 (Sec. 3.2 profile), and the Sec. 4.1 model T = sum(tau_pred N +
         # tau_force n N + tau_corr n) recalibrated with GB300's tau's (Eqs. 1-4).
         eps, eta = 2.0 ** -8, 0.01
+        prec = nb.NB_FP64 if args.precision == "fp64" else nb.NB_MIXED  # (--precision fp64: short --tapp-sizes)
         out = []
         sizes = [int(s) for s in args.tapp_sizes.split(",")]
         for N in sizes:
             m, x, v = inputs.plummer(N, 100 + N)
-            s = nb.NBody(N, nb.NB_MIXED, 0)
+            s = nb.NBody(N, prec, 0)
             s.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
             s.set_j_particles(0, m, x, v)
             s.initial_forces_and_dt()
@@ -574,7 +575,7 @@ def run_integration(args):
             s.close()
             # the host loop again with every block predicting all N first (the on-the-fly j
             # prediction of small blocks, Sec. 4.4 steps 3-4, switched off): the ablation
-            h2 = nb.NBody(N, nb.NB_MIXED, 0)
+            h2 = nb.NBody(N, prec, 0)
             h2.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
             h2.set_j_particles(0, m, x, v)
             h2.initial_forces_and_dt()
@@ -588,7 +589,7 @@ def run_integration(args):
             steps_sep = h2.get_counters()["block_steps"] - ch0["block_steps"]
             h2.close()
             # the same time unit with the whole block-step loop on the device (one CUDA graph)
-            g = nb.NBody(N, nb.NB_MIXED, 0)
+            g = nb.NBody(N, prec, 0)
             g.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
             g.set_j_particles(0, m, x, v)
             g.initial_forces_and_dt()
@@ -602,7 +603,7 @@ def run_integration(args):
             # ... and as one persistent cooperative kernel (systems up to 65536)
             wall_p, drift_p, steps_p = None, None, None
             if N <= nb.NB_PERSISTENT_MAX_N:
-                q = nb.NBody(N, nb.NB_MIXED, 0)
+                q = nb.NBody(N, prec, 0)
                 q.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
                 q.set_j_particles(0, m, x, v)
                 q.initial_forces_and_dt()
@@ -618,8 +619,8 @@ def run_integration(args):
                 q.close()
             # ... and on one thread-block cluster (mixed systems up to 16384)
             wall_c, drift_c, steps_c = None, None, None
-            if N <= nb.NB_CLUSTER_MAX_N:
-                q = nb.NBody(N, nb.NB_MIXED, 0)
+            if N <= nb.NB_CLUSTER_MAX_N and prec == nb.NB_MIXED:
+                q = nb.NBody(N, prec, 0)
                 q.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
                 q.set_j_particles(0, m, x, v)
                 q.initial_forces_and_dt()
@@ -661,7 +662,7 @@ def run_integration(args):
             for r in out:
                 r["model_T_calibrated_at_32768_s"] = sec41_T(taus, r["N"], r["block_steps"], r["interactions"],
                                                              r["particle_steps"])
-        print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": "mixed",
+        print(json.dumps({"workload": "tapp", "eps": eps, "eta": eta, "t_end": 1.0, "precision": args.precision,
                           "grape_tau_force_s": 4.3e-10, "rows": out}), flush=True)
         return
     raise SystemExit(f"unknown workload {w}")

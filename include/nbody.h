@@ -320,18 +320,29 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  *                       hardware barrier separates the phases (three per
  *                       step; no spin wait).  Mixed path only, N <=
  *                       NB_CLUSTER_MAX_N (8192 on an 8-CTA cluster).
- * All three take the same block steps with the same per-particle arithmetic;
+ *   NB_LOOP_AUTO        the driver measured fastest per block step on a GB300
+ *                       for the context's precision and N: the cluster loop
+ *                       for mixed systems of N <= 2048 (where the GPU
+ *                       co-schedules the cluster), the persistent loop up to
+ *                       N = 65536 (mixed) or 2048 (FP64, whose force phase
+ *                       outweighs the step overhead sooner), the host loop
+ *                       beyond.
+ * All of them take the same block steps with the same per-particle arithmetic;
  * sums over j-splits may group differently.  The mixed path renews its
  * spatial order between launches (graph and persistent loops run segments of
  * at most the sort interval).  Errors: NB_EINVAL (t_end, loop, N too large
  * for the persistent loop), NB_ENUMERIC, NB_ETIMEOUT (a bounded device wait
- * gave up; the state is then undefined), NB_ECUDA.  NB_LOOP_CLUSTER: NB_EINVAL
+ * gave up, or the graph loop reached t_end / dt_min + 2 iterations; the state
+ * is then undefined), NB_ESTATE (the block time stopped increasing: a state
+ * without valid steps, e.g. dt = 0 because nb_initial_forces_and_dt was not
+ * called; the host, persistent and cluster loops stop at once), NB_ECUDA.  NB_LOOP_CLUSTER: NB_EINVAL
  * also for the FP64 path or N beyond what the cluster holds.
  */
 #define NB_LOOP_HOST        0
 #define NB_LOOP_GRAPH       1
 #define NB_LOOP_PERSISTENT  2
 #define NB_LOOP_CLUSTER     3
+#define NB_LOOP_AUTO        4
 #define NB_PERSISTENT_MAX_N 65536
 #define NB_CLUSTER_MAX_N    16384
 int nb_integrate(nb_ctx* ctx, double t_end, int loop);

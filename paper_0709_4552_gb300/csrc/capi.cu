@@ -15,6 +15,10 @@ namespace {
 constexpr double kDefaultEps = 1.0 / 256.0;        // Sec. 2: softening 2^-8
 constexpr double kDefaultEta = 0.01;
 constexpr double kDefaultDtMin = 1.0 / 4194304.0;  // Sec. 2: 2^-22
+// NB_LOOP_AUTO's crossovers (block-step loops timed per N on a GB300)
+constexpr int64_t kAutoClusterMaxN = 2048;
+constexpr int64_t kAutoPersistentMaxNMixed = 65536;
+constexpr int64_t kAutoPersistentMaxNFp64 = 2048;
 constexpr double kDefaultDtMax = 0.125;            // Sec. 2: 2^-3
 constexpr size_t kPinnedBytes = 1 << 16;
 // largest block the on-the-fly j prediction takes under NB_JPREDICT_AUTO (the
@@ -321,12 +325,12 @@ int device_status_code(nb_ctx* c, int64_t* underflows) {
   memcpy(&st, c->hpin, sizeof(st));
   if (underflows) *underflows = (int64_t)st.dt_underflows;
   if (st.flags & NB_ST_TIMEOUT) return NB_ETIMEOUT;
+  if (st.flags & NB_ST_STALLED) return NB_ESTATE;  // (before NaNs: the stalled state's corrections make some)
   if (st.flags & NB_ST_NUMERIC) return NB_ENUMERIC;
   if (st.flags & NB_ST_BADLIST) return NB_EINVAL;
   return NB_OK;
 }
 
-// the force rows of the last call to the caller (host copies complete on return)
 // a force call's device outputs, written by the split reduction when there
 // is one; they are cleared when the call returns, on every path
 void set_device_outputs(nb_ctx* c, double* acc, double* jerk, double* pot, int ptr_kind) {
@@ -345,6 +349,7 @@ struct DeviceOutputsScope {
   }
 };
 
+// the force rows of the last call to the caller (host copies complete on return)
 int copy_forces_out(nb_ctx* c, int64_t n, double* acc, double* jerk, double* pot, int ptr_kind) {
   if (ptr_kind == NB_PTR_DEVICE) {  // one launch (none when the split reduction wrote them)
     const bool done = c->fo_done;
@@ -368,6 +373,19 @@ int copy_forces_out(nb_ctx* c, int64_t n, double* acc, double* jerk, double* pot
 }  // namespace
 
 int nb_ensure_sorted(nb_ctx* c) { return ensure_sorted(c); }
+
+// NB_LOOP_AUTO: the driver measured fastest per block step on this GPU for the
+// context's precision and size (one N-body time unit of Plummer spheres): the
+// cluster loop for the smallest mixed systems, the persistent loop while the
+// block steps are latency-bound, the host loop beyond
+static int auto_loop(nb_ctx* c) {
+  if (c->precision == NB_MIXED && c->n <= kAutoClusterMaxN) {
+    const int cs = nb_cluster_size(c);
+    if (cs >= 1 && c->n <= (int64_t)cs * 1024) return NB_LOOP_CLUSTER;
+  }
+  if (c->n <= (c->precision == NB_MIXED ? kAutoPersistentMaxNMixed : kAutoPersistentMaxNFp64)) return NB_LOOP_PERSISTENT;
+  return NB_LOOP_HOST;
+}
 
 // the force dispatcher used by every entry point
 cudaError_t nb_forces(nb_ctx* c, const int32_t* d_list, int64_t n) {
@@ -953,6 +971,10 @@ int nb_step(nb_ctx* c, double* t_out, int64_t* n_out) {
 }
 
 static int integrate_host_loop(nb_ctx* c, double t_end) {
+  // block times strictly increase (every corrected particle moves on by at
+  // least dt_min); a block time that does not is a state without valid steps
+  // (e.g. never initialised: dt = 0), which would otherwise repeat forever
+  double t_prev = -INFINITY;
   for (;;) {
     double t;
     int64_t n;
@@ -961,6 +983,8 @@ static int integrate_host_loop(nb_ctx* c, double t_end) {
     harvest_timings(c);
     if (!isfinite(t) || n <= 0) return fail(c, NB_ENUMERIC);
     if (t > t_end) break;
+    if (!(t > t_prev)) return fail(c, NB_ESTATE);
+    t_prev = t;
     if ((r = step_after_select(c, t, n))) return r;
   }
   return NB_OK;
@@ -974,8 +998,9 @@ int nb_integrate(nb_ctx* c, double t_end, int loop) {
   NB_SINGLE(c);
   if (c->n <= 0) return fail(c, NB_ESTATE);
   if (!(t_end > 0.0) || !isfinite(t_end) || fmod(t_end, c->dt_max) != 0.0) return fail(c, NB_EINVAL);
+  if (loop == NB_LOOP_AUTO) loop = auto_loop(c);
   if (loop != NB_LOOP_HOST && loop != NB_LOOP_GRAPH && loop != NB_LOOP_PERSISTENT && loop != NB_LOOP_CLUSTER)
-    return fail(c, NB_EINVAL);
+    return fail(c, NB_EINVAL);  // (NB_LOOP_AUTO resolved above)
   if (loop == NB_LOOP_PERSISTENT && c->n > NB_PERSISTENT_MAX_N) return fail(c, NB_EINVAL);
   if (loop == NB_LOOP_CLUSTER && (c->n > NB_CLUSTER_MAX_N || c->precision != NB_MIXED)) return fail(c, NB_EINVAL);
   int r = loop == NB_LOOP_GRAPH        ? nb_integrate_graph(c, t_end)
@@ -986,7 +1011,7 @@ int nb_integrate(nb_ctx* c, double t_end, int loop) {
   c->plist_valid = false;
   if (r) return fail(c, r);
   r = device_status_code(c, nullptr);
-  if (r == NB_ENUMERIC || r == NB_ETIMEOUT) return fail(c, r);
+  if (r == NB_ENUMERIC || r == NB_ETIMEOUT || r == NB_ESTATE) return fail(c, r);
   return NB_OK;
 }
 

@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
   const int64_t N = p.N;
   const int nr = own_count(N, me, C);  // <= kCRows (checked by the host)
   long long steps = 0;
+  double tn_prev = -INFINITY;  // the previous block time (they strictly increase)
 
   for (int q = tid; q < nr; q += kCT) {
     const int64_t r = own_row(q, me, C);
@@ -223,6 +224,11 @@ __global__ void __launch_bounds__(kCT, 1) cluster_loop_kernel(ClusterArgs p) {
       break;
     }
     if (tn > p.t_end) break;  // every particle has reached t_end
+    if (!(tn > tn_prev)) {  // no progress: a state without valid steps (dt = 0)
+      if (me == 0 && tid == 0) atomicOr(&p.st->flags, NB_ST_STALLED);
+      break;
+    }
+    tn_prev = tn;
     if (steps >= p.max_steps) {
       if (me == 0 && tid == 0) atomicOr(&p.st->flags, NB_ST_TIMEOUT);
       break;

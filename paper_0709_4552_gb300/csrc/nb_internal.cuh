@@ -42,6 +42,7 @@
 #define NB_ST_NUMERIC 1u
 #define NB_ST_TIMEOUT 2u
 #define NB_ST_BADLIST 4u
+#define NB_ST_STALLED 8u   // a device-driven loop's block time stopped increasing (no valid steps)
 
 struct nb_dev_status {
   unsigned int flags;          // NB_ST_* bits, sticky until cleared

@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(kLT, kLMaxPerSm) loop_kernel(LoopArgs p) {
   const int64_t n_j = jtiles * JT;
   unsigned long long epoch = 0;
   long long steps = 0;
+  double tn_prev = -INFINITY;  // the previous block time (they strictly increase)
 
   // placement: this CTA's rank among the CTAs on its SM.  A step with few
   // force items hands them to rank-0 CTAs first (one per SM), so that they
@@ -490,6 +491,11 @@ __global__ void __launch_bounds__(kLT, kLMaxPerSm) loop_kernel(LoopArgs p) {
       break;
     }
     if (tn > p.t_end) break;  // every particle has reached t_end
+    if (!(tn > tn_prev)) {  // no progress: a state without valid steps (dt = 0)
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&p.st->flags, NB_ST_STALLED);
+      break;
+    }
+    tn_prev = tn;
     if (steps >= p.max_steps) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&p.st->flags, NB_ST_TIMEOUT);
       break;

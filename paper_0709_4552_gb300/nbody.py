@@ -26,7 +26,7 @@ NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ENUMERIC, NB_EDTMIN, NB_ETIMEOUT, NB_E
 NB_FP64, NB_MIXED = 0, 1
 NB_PTR_HOST, NB_PTR_DEVICE = 0, 1
 NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
-NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT, NB_LOOP_CLUSTER = 0, 1, 2, 3
+NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT, NB_LOOP_CLUSTER, NB_LOOP_AUTO = 0, 1, 2, 3, 4
 NB_PERSISTENT_MAX_N = 65536
 NB_CLUSTER_MAX_N = 16384
 NB_JPREDICT_AUTO = -1
@@ -401,8 +401,9 @@ def nb_step(ctx):
 
 
 def nb_integrate(ctx, t_end, use_graph=False, loop=None):
-    """Block steps to t_end.  loop: NB_LOOP_HOST, NB_LOOP_GRAPH or
-    NB_LOOP_PERSISTENT; without it, use_graph picks the graph or host loop."""
+    """Block steps to t_end.  loop: NB_LOOP_HOST, NB_LOOP_GRAPH,
+    NB_LOOP_PERSISTENT, NB_LOOP_CLUSTER or NB_LOOP_AUTO (the fastest for the
+    context's size); without it, use_graph picks the graph or host loop."""
     if loop is None:
         loop = NB_LOOP_GRAPH if use_graph else NB_LOOP_HOST
     _check(lib().nb_integrate(ctx, float(t_end), int(loop)), "nb_integrate")

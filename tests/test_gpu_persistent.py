@@ -138,8 +138,29 @@ def test_persistent_rejects_bad_arguments(nbl):
         assert e.value.code == nbl.NB_EINVAL
         s.clear_error()
         with pytest.raises(nbl.NBodyError) as e:
-            s.integrate(0.125, loop=4)
+            s.integrate(0.125, loop=99)
         assert e.value.code == nbl.NB_EINVAL
+
+
+@pytest.mark.parametrize("loop", ["host", "persistent", "cluster", "auto"])
+def test_state_without_steps_is_refused_promptly(nbl, loop):
+    # particles set but no initial forces and steps (dt = 0): the block time
+    # never advances; every loop driver stops at once with NB_ESTATE instead of
+    # repeating the same block time
+    import time
+    lp = {"host": nbl.NB_LOOP_HOST, "persistent": nbl.NB_LOOP_PERSISTENT, "cluster": nbl.NB_LOOP_CLUSTER,
+          "auto": nbl.NB_LOOP_AUTO}[loop]
+    m, x, v = inputs.plummer(1000, 918)
+    with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
+        s.set_params(1 / 256, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        t0 = time.perf_counter()
+        with pytest.raises(nbl.NBodyError) as e:
+            s.integrate(0.125, loop=lp)
+        if loop == "cluster" and e.value.code == nbl.NB_ECUDA:
+            pytest.skip("this GPU does not co-schedule the cluster")
+        assert e.value.code == nbl.NB_ESTATE
+        assert time.perf_counter() - t0 < 10.0
 
 
 def test_grid_barrier_wait_is_bounded(nbl):
@@ -176,3 +197,24 @@ def test_strict_differences_in_every_loop(nbl, loop):
     assert abs(cb - ca) <= 0.05 * ca
     assert np.mean(a["dt"] == b["dt"]) > 0.95
     assert np.abs(a["x"] - b["x"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("prec_name,N,expect", [("mixed", 1024, "cluster"), ("mixed", 3000, "persistent"),
+                                                 ("fp64", 1000, "persistent"), ("mixed", 70000, "host")])
+def test_auto_loop_takes_the_measured_driver(nbl, prec_name, N, expect):
+    # NB_LOOP_AUTO resolves to one of the explicit drivers: its run repeats that
+    # driver's run bit for bit (the cluster loop where the GPU co-schedules it)
+    prec = nbl.NB_MIXED if prec_name == "mixed" else nbl.NB_FP64
+    loop = {"cluster": nbl.NB_LOOP_CLUSTER, "persistent": nbl.NB_LOOP_PERSISTENT, "host": nbl.NB_LOOP_HOST}[expect]
+    t_end = 2.0 ** -8 if N > 10000 else 2.0 ** -5
+    ics = inputs.plummer(N, 31)
+    try:
+        ref, cr = _run(nbl, prec, ics, 1 / 256, t_end, [(t_end, loop)])
+    except nbl.NBodyError:
+        if expect == "cluster":
+            pytest.skip("this GPU does not co-schedule the cluster")
+        raise
+    got, cg = _run(nbl, prec, ics, 1 / 256, t_end, [(t_end, nbl.NB_LOOP_AUTO)])
+    assert cg["block_steps"] == cr["block_steps"]
+    for k in ("x", "v", "a", "jerk", "t", "dt"):
+        assert np.array_equal(got[k], ref[k]), k
