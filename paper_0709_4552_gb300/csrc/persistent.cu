@@ -506,20 +506,25 @@ __global__ void __launch_bounds__(kLT, kLMaxPerSm) loop_kernel(LoopArgs p) {
     if (!grid_barrier(p.ctl, epoch, G, p.st, &s.ok)) return;  // B: list and j-store complete
 
     // forces (Sec. 4.1 step 4): items i-tile x j-split from the step's
-    // counter, taken by the CTAs of rank < ceil(items / SMs)
+    // counter, taken by the CTAs of rank < ceil(items / SMs).  When every CTA
+    // has an SM of its own and there are no more items than CTAs (every small
+    // block), CTA b takes item b: no counter round trips at all.
     const int64_t nI = (n + kLT - 1) / kLT;
     const int64_t S = loop_splits(n, jtiles, G, p.part_elems);
     const int64_t pstride = ((n + 31) / 32) * 32;
     const bool fin = S == 1;
     const int items = (int)(nI * S);
     const unsigned int nsm = __ldcg(&p.ctl->nsm);
-    const bool takes = (int64_t)s.rank * nsm < items;
-    for (;;) {
-      if (!takes) break;
-      __syncthreads();  // every thread has read the previous item
-      if (threadIdx.x == 0) s.item = (long long)atomicAdd(&p.ctl->wq, 1ULL);
-      __syncthreads();
-      const int item = (int)min(s.item, (long long)items);
+    const bool fixed = nsm == G && items <= (int)G;
+    const bool takes = fixed ? (int)blockIdx.x < items : (int64_t)s.rank * nsm < items;
+    for (int round = 0;; ++round) {
+      if (!takes || (fixed && round > 0)) break;
+      if (!fixed) {
+        __syncthreads();  // every thread has read the previous item
+        if (threadIdx.x == 0) s.item = (long long)atomicAdd(&p.ctl->wq, 1ULL);
+        __syncthreads();
+      }
+      const int item = fixed ? (int)blockIdx.x : (int)min(s.item, (long long)items);
       if (item >= items) break;
       const int itile = item % (int)nI, split = item / (int)nI;
       const int64_t jlo = nbk::split_begin(split, S, jtiles) * JT;
