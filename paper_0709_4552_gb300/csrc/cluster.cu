@@ -8,24 +8,27 @@
 // and keep them in shared memory, predicted to each block time on
 // the fly from the j-memory (the GRAPE-style double-single records of
 // onboard.cu, Sec. 4.4 step 4).  Per block step (Sec. 4.1 steps 2-5):
-//   A  every CTA has published the minimum of t_i + dt_i over its rows and
-//      how many rows reach it; each reads all C pairs from the others' shared
-//      memory (distributed shared memory), takes the block time and its
-//      offset in the active list, lists its active rows, predicts them in
-//      FP64 (step 3; kept for the corrector) and as double-single i data, and
-//      predicts its j rows on the fly;
-//   B  the active block, in groups of 256: each CTA gathers the group's i data
-//      from the owners' shared memory and sums the forces of its own j rows
-//      on it (step 4, Eq. 3: FP32 pairwise arithmetic on double-single
-//      differences, per-chunk FP32 sums folded into double-single, the self
-//      pair excluded by row);
-//   C  each owner adds the C partial sums of its particles in CTA order and
-//      corrects them (step 5; the four-lane corrector of hermite.cuh), then
-//      rewrites their j-memory records and publishes its next minimum.
+//   A  every CTA has pushed the minimum of t_i + dt_i over its rows and how
+//      many rows reach it into every CTA's shared memory (distributed shared
+//      memory); each takes the block time and its offset in the active list,
+//      lists its active rows, predicts them in FP64 (step 3; the corrector's
+//      inputs stay in shared memory) and as double-single i data, while other
+//      warps predict its j rows on the fly, and pushes its particles of the
+//      first force group into every CTA;
+//   B  the active block, in groups of 256 (later groups gathered from the
+//      owners): each CTA sums the forces of its own j rows on the group (step
+//      4, Eq. 3: FP32 pairwise arithmetic on double-single differences in
+//      packed FP32x2 pairs, per-chunk FP32 sums folded into double-single, the
+//      self pair excluded by row), partials reduced in double-single FP32;
+//   C  each owner adds the C double-single partial sums of its particles in
+//      CTA order and corrects them (step 5; the four-lane corrector of
+//      hermite.cuh, which also rewrites their j-memory records), then pushes
+//      its next minimum.
 // The barriers are the cluster's hardware barrier (no spin loop anywhere);
 // every CTA reads the same published values, so every CTA takes the same
-// decisions and leaves the loop at the same step.  Nothing leaves the chip
-// but the state each owner writes back.
+// decisions and leaves the loop at the same step (and a last barrier keeps
+// every CTA's shared memory alive while others may read it).  Nothing
+// leaves the chip but the state each owner writes back.
 #include <cooperative_groups.h>
 #include <float.h>
 #include <math.h>

@@ -13,12 +13,15 @@
 //     (ascending), predicts its own rows to t (step 3) and, on the mixed path
 //     in spatial order, computes the boxes of its own tiles.    -> barrier B
 //   phase 2: force items (i-tile of 128 list positions x j-split) taken from
-//     a work counter (step 4, Eq. 3), the same items as the host-driven
-//     kernels.                                                    -> barrier C
+//     a work counter, or by block index when every CTA has an SM of its own
+//     and the items fit (step 4, Eq. 3), the same items as the host-driven
+//     kernels, split partials as double-single pairs.            -> barrier C
 //   phase 3: every CTA sums the j-splits of its own list positions in a fixed
-//     order, corrects them and picks their new steps (step 5), then
-//     publishes the minimum of t_i + dt_i over its rows and how many rows
-//     reach it.                                                   -> barrier A
+//     order (double-single FP32), corrects them and picks their new steps
+//     (step 5; own rows' due times kept in shared memory), then publishes the
+//     minimum of t_i + dt_i over its rows and how many rows reach it; a block
+//     time that does not increase stops the loop (no valid steps).
+//                                                                 -> barrier A
 // The active block is exactly the rows at the global minimum, so a CTA whose
 // own minimum is larger has none, and the counts published with the minima
 // give every CTA its list offset without a further barrier.
