@@ -335,7 +335,7 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  * gave up, or the graph loop reached t_end / dt_min + 2 iterations; the state
  * is then undefined), NB_ESTATE (the block time stopped increasing: a state
  * without valid steps, e.g. dt = 0 because nb_initial_forces_and_dt was not
- * called; the host, persistent and cluster loops stop at once), NB_ECUDA.  NB_LOOP_CLUSTER: NB_EINVAL
+ * called; every loop stops within two block steps), NB_ECUDA.  NB_LOOP_CLUSTER: NB_EINVAL
  * also for the FP64 path or N beyond what the cluster holds.
  */
 #define NB_LOOP_HOST        0

@@ -140,11 +140,15 @@ __device__ __forceinline__ double cluster_tmin(const unsigned long long* ch_min,
   return __longlong_as_double((long long)best);
 }
 
+// (also: an active cluster's block time must exceed the one it had at the
+// previous iteration of this launch, else the state has no valid steps, e.g.
+// dt = 0: NB_ST_STALLED, and the plan ends the loop)
 __global__ void b_sel_count(const int32_t* __restrict__ ch_cluster, const int64_t* __restrict__ lo,
                             const int64_t* __restrict__ hi, const int32_t* __restrict__ cl_ch0,
                             const unsigned long long* __restrict__ ch_min, const double* __restrict__ ti,
                             const double* __restrict__ dt, double* __restrict__ tnext,
-                            int32_t* __restrict__ ch_cnt) {
+                            int32_t* __restrict__ ch_cnt, const int64_t* __restrict__ ctrl,
+                            const BParams* __restrict__ prm, nb_dev_status* __restrict__ st) {
   const int j = blockIdx.x;
   const int c = ch_cluster[j];
   __shared__ double tn;
@@ -152,7 +156,10 @@ __global__ void b_sel_count(const int32_t* __restrict__ ch_cluster, const int64_
     const double t = cluster_tmin(ch_min, cl_ch0[c], cl_ch0[c + 1]);
     if (threadIdx.x == 0) {
       tn = t;
-      if (j == cl_ch0[c]) tnext[c] = t;
+      if (j == cl_ch0[c]) {
+        if (ctrl[1] > 0 && t <= prm->t_end && !(t > tnext[c])) atomicOr(&st->flags, NB_ST_STALLED);
+        tnext[c] = t;
+      }
     }
   }
   __syncthreads();
@@ -347,6 +354,7 @@ __global__ void b_plan(int32_t C, const int64_t* __restrict__ off, const int32_t
     ctrl[1] = iters;
     ctrl[2] += tot_i;
     int go = tot_a > 0;
+    if (go && (st->flags & NB_ST_STALLED)) go = 0;  // a block time did not advance (b_sel_count)
     if (go && iters > prm->max_iters) {
       atomicOr(&st->flags, NB_ST_TIMEOUT);
       go = 0;
@@ -922,7 +930,7 @@ cudaError_t capture_step(nb_ctx* c, Batch* b, cudaGraphConditionalHandle handle,
   const int grid = mixed ? b->grid_mixed : b->grid_fp64;
   b_sel_min<<<b->nchunks, 256, 0, c->stream>>>(b->ch_lo, b->ch_hi, c->t, c->dt, b->ch_min);
   b_sel_count<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_min, c->t,
-                                                 c->dt, b->tnext, b->ch_cnt);
+                                                 c->dt, b->tnext, b->ch_cnt, b->ctrl, b->prm, c->status);
   b_sel_write<<<b->nchunks, 256, 0, c->stream>>>(b->ch_cluster, b->ch_lo, b->ch_hi, b->cl_ch0, b->ch_cnt, b->off,
                                                  c->t, c->dt, b->tnext, b->prm, c->act, b->nact);
   b_plan<<<1, 1024, 0, c->stream>>>(b->C, b->off, b->nact, per_cta, jt, b->waves * (int64_t)grid, c->part_elems,
@@ -997,6 +1005,7 @@ int finish_status(nb_ctx* c) {
     return NB_ECUDA;
   memcpy(&st, c->hpin, sizeof(st));
   if (st.flags & NB_ST_TIMEOUT) return NB_ETIMEOUT;
+  if (st.flags & NB_ST_STALLED) return NB_ESTATE;  // (before NaNs: the stalled state's corrections make some)
   if (st.flags & NB_ST_NUMERIC) return NB_ENUMERIC;
   return NB_OK;
 }

@@ -142,14 +142,14 @@ def test_persistent_rejects_bad_arguments(nbl):
         assert e.value.code == nbl.NB_EINVAL
 
 
-@pytest.mark.parametrize("loop", ["host", "persistent", "cluster", "auto"])
+@pytest.mark.parametrize("loop", ["host", "graph", "persistent", "cluster", "auto"])
 def test_state_without_steps_is_refused_promptly(nbl, loop):
     # particles set but no initial forces and steps (dt = 0): the block time
     # never advances; every loop driver stops at once with NB_ESTATE instead of
     # repeating the same block time
     import time
-    lp = {"host": nbl.NB_LOOP_HOST, "persistent": nbl.NB_LOOP_PERSISTENT, "cluster": nbl.NB_LOOP_CLUSTER,
-          "auto": nbl.NB_LOOP_AUTO}[loop]
+    lp = {"host": nbl.NB_LOOP_HOST, "graph": nbl.NB_LOOP_GRAPH, "persistent": nbl.NB_LOOP_PERSISTENT,
+          "cluster": nbl.NB_LOOP_CLUSTER, "auto": nbl.NB_LOOP_AUTO}[loop]
     m, x, v = inputs.plummer(1000, 918)
     with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
         s.set_params(1 / 256, 0.01, 2.0 ** -22, 2.0 ** -3)
