@@ -15,11 +15,11 @@ namespace {
 constexpr double kDefaultEps = 1.0 / 256.0;        // Sec. 2: softening 2^-8
 constexpr double kDefaultEta = 0.01;
 constexpr double kDefaultDtMin = 1.0 / 4194304.0;  // Sec. 2: 2^-22
+constexpr double kDefaultDtMax = 0.125;            // Sec. 2: 2^-3
 // NB_LOOP_AUTO's crossovers (block-step loops timed per N on a GB300)
 constexpr int64_t kAutoClusterMaxN = 2048;
 constexpr int64_t kAutoPersistentMaxNMixed = 65536;
 constexpr int64_t kAutoPersistentMaxNFp64 = 2048;
-constexpr double kDefaultDtMax = 0.125;            // Sec. 2: 2^-3
 constexpr size_t kPinnedBytes = 1 << 16;
 // largest block the on-the-fly j prediction takes under NB_JPREDICT_AUTO (the
 // default): measured on a GB300 at N = 2^20, the in-kernel prediction costs
