@@ -96,6 +96,26 @@ def test_autotune_on_a_caller_list(nbl, monkeypatch):
             s.autotune_list(idx[::-1].copy())
 
 
+@pytest.mark.parametrize("n", [1, 33, 2000])
+def test_autotune_list_edge_sizes(nbl, monkeypatch, n):
+    # one particle, a ragged warp, the whole system: a supported launch comes
+    # back and the tuned forces still match the oracle
+    monkeypatch.setenv("NB_TUNE_FILE", "")
+    N, eps = 2000, 1.0 / 256
+    m, x, v = inputs.plummer(N, 53)
+    idx = (np.arange(N) if n == N else inputs.sample_indices(N, n, 10)).astype(np.int32)
+    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+        s.set_params(eps, 0.01, 2.0 ** -22, 2.0 ** -3)
+        s.set_j_particles(0, m, x, v)
+        s.predict(0.0)
+        cfg = s.autotune_list(idx)
+        assert cfg["threads"] in (64, 128, 256) and 0 <= cfg["n_split"] <= 4096
+        a, j, p = s.compute_forces(idx)
+    ref = oracle.forces(m, x, v, eps, idx=idx.astype(np.int64), compensated=True)
+    ea = np.linalg.norm(a - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+
+
 def test_table_refuses_foreign_or_broken_files(nbl, tmp_path, monkeypatch):
     monkeypatch.setenv("NB_TUNE_FILE", "")
     with nbl.NBody(1000, nbl.NB_MIXED, 0) as s:
