@@ -42,12 +42,12 @@ namespace {
 
 constexpr int kLT = 128;                     // threads per CTA = i-tile = row tile
 constexpr int kLWarps = kLT / 32;
-constexpr int kLMaxPerSm = 3;                // resident CTAs per SM asked for (160 registers)
+constexpr int kLMaxPerSm = 4;                // resident CTAs per SM asked for (128 registers)
 constexpr int kLMixJT = 128, kLF64JT = 64;   // j-tiles (the mixed one = the box tile)
 constexpr long long kWaitNs = 4000000000LL;  // a barrier wait of the loop gives up after 4 s
 constexpr unsigned int kPollCap = 1u << 26;  // ... or after this many polls
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;  // +inf
-constexpr int kLItemWaves = 4;               // force items per step: about 4 per CTA ...
+constexpr int kLItemWaves = 2;               // force items per step: about 2 per CTA ...
 constexpr int64_t kLMaxSplits = 256;         // ... with at most this many j-splits
 constexpr int kMaxSmid = 1024;               // SM ids counted by the CTA placement
 
