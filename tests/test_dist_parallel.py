@@ -94,3 +94,26 @@ def test_ring_algorithm_matches_one_rank(orc):
     assert out[0]["steps"] == out[1]["steps"] == ref["block_steps"]
     assert np.array_equal(t, ref["t"]) and np.array_equal(dt, ref["dt"])
     assert np.abs(x - ref["x"]).max() < 1e-12
+
+
+def test_fence_orders_streams_only_where_needed():
+    # _fence: nothing for host tensors or an engine on torch's current stream,
+    # a device synchronisation for an engine on a stream of its own
+    from types import SimpleNamespace
+    from paper_0709_4552_gb300 import distributed as D
+
+    calls = []
+    cur = SimpleNamespace(cuda_stream=1234)
+    fake_torch = SimpleNamespace(cuda=SimpleNamespace(current_stream=lambda dev: cur,
+                                                      synchronize=lambda dev: calls.append(dev)))
+
+    def comm(kind):
+        return SimpleNamespace(device=SimpleNamespace(type=kind), torch=fake_torch)
+
+    D._fence(SimpleNamespace(stream_handle=None), comm("cpu"))
+    D._fence(SimpleNamespace(stream_handle=1234), comm("cuda"))
+    assert calls == []
+    D._fence(SimpleNamespace(stream_handle=None), comm("cuda"))
+    D._fence(SimpleNamespace(stream_handle=99), comm("cuda"))
+    D._fence(SimpleNamespace(), comm("cuda"))
+    assert len(calls) == 3
