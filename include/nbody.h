@@ -373,7 +373,9 @@ int nb_get_counters(nb_ctx* ctx, int64_t* kernel_launches, int64_t* block_steps)
 /*
  * nb_check_device_status -- synchronise and read the device-side status
  * word: NaN/Inf seen (NB_ENUMERIC), step criterion below dt_min (count in
- * *dt_underflows, may be NULL), bounded wait timeout (NB_ETIMEOUT).
+ * *dt_underflows, may be NULL), bounded wait timeout (NB_ETIMEOUT), a
+ * device-driven loop whose block time stopped increasing (NB_ESTATE), a bad
+ * device list (NB_EINVAL).  Bits stay set until nb_clear_error.
  */
 int nb_check_device_status(nb_ctx* ctx, int64_t* dt_underflows);
 
