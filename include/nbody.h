@@ -574,9 +574,10 @@ int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
  * jerk[n][3], pot[n] (any may be NULL).  The indices are not checked (that
  * would need a status word the caller reads back): an index below 0 or
  * >= N is clamped to 0 or N - 1 for every read, so no access leaves the
- * caller's arrays, and the outputs at that list position are unspecified.  Work is enqueued on cuda_stream (a cudaStream_t, NULL = default
- * stream); the call returns without synchronising.  It calls no cudaMalloc,
- * cudaFree or allocating library routine.
+ * caller's arrays, and the outputs at that list position are unspecified.
+ * Work is enqueued on cuda_stream (a cudaStream_t, NULL = default stream);
+ * the call returns without synchronising.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
  *
  * Split-j partial sums use one fixed array inside the library
  * (NB_NOALLOC_SCRATCH_DOUBLES doubles, kept on every GPU that loads the
@@ -586,10 +587,10 @@ int nb_ensemble_energy(nb_ctx* ctx, double* ekin, double* epot);
  * before any stream capture.  The address is remembered with the id of the
  * CUDA context it belongs to; after a device reset the next call repeats the
  * look-up (so, after a reset, make one call before any capture again).  All
- * calls share the array, which keeps the
- * previous call's contents (every partial is written before it is read, so
- * nothing needs clearing): calls whose work may overlap on the GPU race and
- * must be ordered by the caller (one stream, or events).
+ * calls share the array, which keeps the previous call's contents (every
+ * partial is written before it is read, so nothing needs clearing): calls
+ * whose work may overlap on the GPU race and must be ordered by the caller
+ * (one stream, or events).
  * Errors: NB_EINVAL (N < 1, n < 0, n > N, n > NB_NOALLOC_MAX_ACTIVE -- the
  * partial sums would not fit --, NULL inputs, eps < 0), NB_ECUDA.
  */
