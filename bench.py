@@ -600,9 +600,9 @@ def run_integration(args):
             wall_g = time.perf_counter() - t0
             kg, wg = g.energy()
             g.close()
-            # ... and as one persistent cooperative kernel (systems up to 65536)
+            # ... and as one persistent cooperative kernel (mixed systems up to 262144, FP64 up to 65536)
             wall_p, drift_p, steps_p = None, None, None
-            if N <= nb.NB_PERSISTENT_MAX_N:
+            if N <= (nb.NB_PERSISTENT_MAX_N if prec == nb.NB_MIXED else nb.NB_PERSISTENT_MAX_N_FP64):
                 q = nb.NBody(N, prec, 0)
                 q.set_params(eps, eta, 2.0 ** -22, 2.0 ** -3)
                 q.set_j_particles(0, m, x, v)

@@ -310,7 +310,11 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  *   NB_LOOP_PERSISTENT  one cooperative kernel that stays resident for the
  *                       whole run (a few CTAs per SM, three grid barriers per
  *                       block step, each wait bounded), for systems whose
- *                       block steps are latency-bound: N <= NB_PERSISTENT_MAX_N.
+ *                       block steps are latency-bound: N <= NB_PERSISTENT_MAX_N
+ *                       on the mixed path, N <= NB_PERSISTENT_MAX_N_FP64 on
+ *                       the FP64 path (a full-block force phase must stay
+ *                       far inside the 4 s barrier wait: ~70 ms for 2^18
+ *                       mixed particles, ~0.3 s for 2^16 in FP64).
  *   NB_LOOP_CLUSTER     one thread-block cluster (16 CTAs, one per SM; 8 where
  *                       the GPU cannot co-schedule 16) for the whole run, the
  *                       ring algorithm of Sec. 4.3 on one chip: each CTA holds
@@ -324,14 +328,14 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
  *                       for the context's precision and N: the cluster loop
  *                       for mixed systems of N <= 2048 (where the GPU
  *                       co-schedules the cluster), the persistent loop up to
- *                       N = 65536 (mixed) or 2048 (FP64, whose force phase
+ *                       N = 131072 (mixed) or 2048 (FP64, whose force phase
  *                       outweighs the step overhead sooner), the host loop
  *                       beyond.
  * All of them take the same block steps with the same per-particle arithmetic;
  * sums over j-splits may group differently.  The mixed path renews its
  * spatial order between launches (graph and persistent loops run segments of
  * at most the sort interval).  Errors: NB_EINVAL (t_end, loop, N too large
- * for the persistent loop), NB_ENUMERIC, NB_ETIMEOUT (a bounded device wait
+ * for the persistent loop at the context's precision), NB_ENUMERIC, NB_ETIMEOUT (a bounded device wait
  * gave up, or the graph loop reached t_end / dt_min + 2 iterations; the state
  * is then undefined), NB_ESTATE (the block time stopped increasing: a state
  * without valid steps, e.g. dt = 0 because nb_initial_forces_and_dt was not
@@ -343,7 +347,8 @@ int nb_step(nb_ctx* ctx, double* t_out, int64_t* n_active_out);
 #define NB_LOOP_PERSISTENT  2
 #define NB_LOOP_CLUSTER     3
 #define NB_LOOP_AUTO        4
-#define NB_PERSISTENT_MAX_N 65536
+#define NB_PERSISTENT_MAX_N 262144
+#define NB_PERSISTENT_MAX_N_FP64 65536
 #define NB_CLUSTER_MAX_N    16384
 int nb_integrate(nb_ctx* ctx, double t_end, int loop);
 

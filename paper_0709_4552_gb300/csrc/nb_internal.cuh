@@ -278,6 +278,11 @@ int nb_cluster_size(nb_ctx* c);  // CTAs per cluster the GPU co-schedules (16, 8
 // persistent.cu: the block-step loop of one system as one cooperative launch
 int nb_integrate_persistent(nb_ctx* c, double t_end);
 void nb_persistent_free(nb_ctx* c);
+// largest N the loop takes at the context's precision (a full-block force
+// phase stays far inside the barrier wait)
+inline int64_t nb_persistent_max_n(const nb_ctx* c) {
+  return c->precision == NB_MIXED ? NB_PERSISTENT_MAX_N : NB_PERSISTENT_MAX_N_FP64;
+}
 // the grid barrier's bounded wait (phantom: wait for one CTA more than launched)
 int nb_persistent_barrier_check(nb_ctx* c, int phantom, double wait_ms);
 

@@ -604,7 +604,7 @@ void nb_persistent_free(nb_ctx* c) {
 }
 
 int nb_integrate_persistent(nb_ctx* c, double t_end) {
-  if (c->n > NB_PERSISTENT_MAX_N) return NB_EINVAL;
+  if (c->n > nb_persistent_max_n(c)) return NB_EINVAL;
   const bool mixed = c->precision == NB_MIXED;
   PLoop* L = ploop_of(c);
   if (!L) {

@@ -27,7 +27,7 @@ NB_FP64, NB_MIXED = 0, 1
 NB_PTR_HOST, NB_PTR_DEVICE = 0, 1
 NB_ENSEMBLE_PERSISTENT, NB_ENSEMBLE_PER_CLUSTER = 0, 1
 NB_LOOP_HOST, NB_LOOP_GRAPH, NB_LOOP_PERSISTENT, NB_LOOP_CLUSTER, NB_LOOP_AUTO = 0, 1, 2, 3, 4
-NB_PERSISTENT_MAX_N = 65536
+NB_PERSISTENT_MAX_N, NB_PERSISTENT_MAX_N_FP64 = 262144, 65536
 NB_CLUSTER_MAX_N = 16384
 NB_JPREDICT_AUTO = -1
 

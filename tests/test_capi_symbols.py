@@ -45,7 +45,8 @@ def test_binding_constants_match_header():
     defs = dict(re.findall(r"#define\s+(NB_[A-Z0-9_]+)\s+(-?\d+)\b", src))
     names = [n for n in defs if hasattr(nbody, n)]
     for must in ("NB_OK", "NB_ETIMEOUT", "NB_FP64", "NB_MIXED", "NB_LOOP_HOST", "NB_LOOP_GRAPH",
-                 "NB_LOOP_PERSISTENT", "NB_PERSISTENT_MAX_N", "NB_ENSEMBLE_PER_CLUSTER"):
+                 "NB_LOOP_PERSISTENT", "NB_PERSISTENT_MAX_N", "NB_PERSISTENT_MAX_N_FP64",
+                 "NB_ENSEMBLE_PER_CLUSTER"):
         assert must in names
     for n in names:
         assert getattr(nbody, n) == int(defs[n]), n

@@ -67,11 +67,14 @@ def test_loops_bitwise_equal_when_sums_group_alike(nbl, N):
             assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("N", [1500, 6000])
+@pytest.mark.parametrize("N", [1500, 6000, 131072])
 def test_persistent_mixed_matches_host_loop(nbl, N):
-    # several launches: the spatial order is renewed every 64 block steps
-    ics = inputs.plummer(N, 700 + N, "salpeter")
-    eps, t_end = 1 / 256, 2.0 ** -5
+    # several launches: the spatial order is renewed every 64 block steps;
+    # 131072 lies above the FP64 loop's bound (a few hundred rows per CTA,
+    # full-block force phases of 1.7e10 interactions)
+    big = N > nbl.NB_PERSISTENT_MAX_N_FP64
+    ics = inputs.plummer(N, 700 + N, "equal" if big else "salpeter")
+    eps, t_end = 1 / 256, 2.0 ** (-7 if big else -5)
     a, ca = _run(nbl, nbl.NB_MIXED, ics, eps, t_end, [(t_end, nbl.NB_LOOP_HOST)])
     b, cb = _run(nbl, nbl.NB_MIXED, ics, eps, t_end, [(t_end, nbl.NB_LOOP_PERSISTENT)])
     assert np.all(a["t"] == t_end) and np.all(b["t"] == t_end)
@@ -127,13 +130,17 @@ def test_persistent_numeric_failure_reported(nbl):
         assert s.check_device_status()[0] == nbl.NB_OK
 
 
-def test_persistent_rejects_bad_arguments(nbl):
-    N = nbl.NB_PERSISTENT_MAX_N + 1
+@pytest.mark.parametrize("prec_name", ["mixed", "fp64"])
+def test_persistent_rejects_bad_arguments(nbl, prec_name):
+    # one particle above the precision's bound: a full-block force phase
+    # would come too close to the barrier wait's limit
+    prec = nbl.NB_MIXED if prec_name == "mixed" else nbl.NB_FP64
+    N = (nbl.NB_PERSISTENT_MAX_N if prec == nbl.NB_MIXED else nbl.NB_PERSISTENT_MAX_N_FP64) + 1
     m, x, v = inputs.plummer(N, 917)
-    with nbl.NBody(N, nbl.NB_MIXED, 0) as s:
+    with nbl.NBody(N, prec, 0) as s:
         s.set_params(1 / 256, 0.01, 2.0 ** -22, 2.0 ** -3)
         s.set_j_particles(0, m, x, v)
-        with pytest.raises(nbl.NBodyError) as e:   # too large for one cooperative launch's barriers
+        with pytest.raises(nbl.NBodyError) as e:
             s.integrate(0.125, loop=nbl.NB_LOOP_PERSISTENT)
         assert e.value.code == nbl.NB_EINVAL
         s.clear_error()
@@ -200,7 +207,8 @@ def test_strict_differences_in_every_loop(nbl, loop):
 
 
 @pytest.mark.parametrize("prec_name,N,expect", [("mixed", 1024, "cluster"), ("mixed", 3000, "persistent"),
-                                                 ("fp64", 1000, "persistent"), ("mixed", 70000, "host")])
+                                                 ("fp64", 1000, "persistent"), ("fp64", 3000, "host"),
+                                                 ("mixed", 70000, "persistent"), ("mixed", 140000, "host")])
 def test_auto_loop_takes_the_measured_driver(nbl, prec_name, N, expect):
     # NB_LOOP_AUTO resolves to one of the explicit drivers: its run repeats that
     # driver's run bit for bit (the cluster loop where the GPU co-schedules it)
